@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Throughput of the fused single-array regularized lattice Boltzmann step.
+
+Metric: MLUPS (million lattice-node updates per second, the paper's GLUPS x
+1e3) on one GB300, with the dominant kernel's fraction of the HBM roofline.
+Default workload: D3Q19 lid-driven cavity, 1024^3 nodes (one FP32 population
+array, 81.6 GB), tau = 0.52, lid velocity 0.05, started from rest.
+
+A step is one time step over the whole grid (one launch of the fused kernel).
+The grid (81.6 GB) is far larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(replicas only: the single-domain step has no multi-GPU path here) and rank 0
+prints the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: lattice, dims, tau, boundary kind, parameters
+    "cavity_d3q19_1024": dict(lattice="D3Q19", dims=(1024, 1024, 1024), tau=0.52, flow="cavity", lid=0.05),
+    "cavity_d3q19_512": dict(lattice="D3Q19", dims=(512, 512, 512), tau=0.52, flow="cavity", lid=0.05),
+    "cavity_d3q19_256": dict(lattice="D3Q19", dims=(256, 256, 256), tau=0.52, flow="cavity", lid=0.05),
+    "tg_d3q27_512": dict(lattice="D3Q27", dims=(512, 512, 512), tau=0.8, flow="tg3d", u0=0.02),
+    "tg_d3q27_256": dict(lattice="D3Q27", dims=(256, 256, 256), tau=0.8, flow="tg3d", u0=0.02),
+    "tg_d2q9_16384": dict(lattice="D2Q9", dims=(16384, 16384, 1), tau=0.8, flow="tg2d", u0=0.01),
+}
+Q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}
+STORAGE_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}
+
+
+def boundary(w):
+    if w["flow"] == "cavity":
+        faces = [1, 1, 1, 2, 1, 1]
+        wall_u = [[0, 0, 0]] * 3 + [[w["lid"], 0, 0]] + [[0, 0, 0]] * 2
+        return faces, wall_u
+    return [0] * 6, None
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def read_traffic(kernel_key):
+    """DRAM bytes per node update measured by ncu (profiles/*.txt), or None."""
+    p = os.path.join(ROOT, "profiles", "traffic_per_update.txt")
+    try:
+        for line in open(p):
+            line = line.strip()
+            if line.startswith(kernel_key + " "):
+                return float(line.split()[1])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        exe = shutil.which("nvidia-smi")
+        if not exe:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        self.fh = open(self.path, "w")
+        self.proc = subprocess.Popen([exe, "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                      "-i", str(self.dev), "-lms", "200"], stdout=self.fh,
+                                     stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_state(solver, w, torch):
+    """Synthetic initial condition, generated on the device."""
+    if w["flow"] == "cavity":
+        solver.init_uniform(1.0, (0.0, 0.0, 0.0))
+        return
+    import synth
+    if w["flow"] == "tg3d":
+        rho, u, pi = synth.taylor_green_3d_torch(w["dims"][0], w["u0"], 1.0, w["tau"], torch)
+    else:
+        rho, u, pi = synth.taylor_green_2d_torch(w["dims"][0], w["u0"], 1.0, w["tau"], torch)
+    solver.init_moments(rho, u, pi)
+    del rho, u, pi
+    torch.cuda.empty_cache()
+
+
+def cpu_oracle_rate(lattice, budget_s=12.0, n=80, tau=0.52, lid=0.05, threads=0):
+    """The FP64 CPU oracle on a bounded sample of the workload (cavity cube of side n)."""
+    import oracle
+    import synth
+    faces = [1, 1, 1, 2, 1, 1]
+    wall_u = [[0, 0, 0]] * 3 + [[lid, 0, 0]] + [[0, 0, 0]] * 2
+    dims = (n, n, n) if lattice != "D2Q9" else (n * 8, n * 8, 1)
+    if lattice == "D2Q9":
+        faces = faces[:4] + [0, 0]
+    cfg = oracle.make_cfg(lattice, dims, tau, faces=faces, wall_u=wall_u)
+    rho, u = synth.rest_state(dims, 2 if lattice == "D2Q9" else 3)
+    f = oracle.init(cfg, rho, u)
+    N = dims[0] * dims[1] * dims[2]
+    f = oracle.run(cfg, f, 1, threads)  # warm
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        f = oracle.run(cfg, f, 1, threads)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    used = threads if threads > 0 else oracle.max_threads()
+    return N * steps / dt / 1e6, used, "%s lid-driven cavity %s, %d steps from rest (FP64 oracle, two arrays)" % (
+        lattice, "x".join(map(str, dims)), steps)
+
+
+def run_reference(args, w):
+    """--impl reference: the CPU oracle, timed on a bounded sample of the workload."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    lattice = w["lattice"]
+    n = 64
+    dims = (n, n, n) if lattice != "D2Q9" else (1024, 1024, 1)
+    faces, wall_u = boundary(w)
+    if lattice == "D2Q9":
+        faces = faces[:4] + [0, 0]
+    cfg = oracle.make_cfg(lattice, dims, w["tau"], faces=faces, wall_u=wall_u)
+    d = 2 if lattice == "D2Q9" else 3
+    rho, u = synth.rest_state(dims, d)
+    f = oracle.init(cfg, rho, u)
+    f = oracle.run(cfg, f, args.warmup)
+    t0 = time.perf_counter()
+    f = oracle.run(cfg, f, args.steps)
+    dt = time.perf_counter() - t0
+    N = dims[0] * dims[1] * dims[2]
+    value = N * args.steps / dt / 1e6
+    cores = oracle.max_threads()
+    sample = "%s %s, %d timed steps (FP64 CPU oracle, two arrays, OpenMP)" % (lattice, "x".join(map(str, dims)),
+                                                                          args.steps)
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cavity_d3q19_1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--storage", default="f32", choices=sorted(STORAGE_BYTES))
+    ap.add_argument("--scheme", default="fused", choices=["fused", "two_pass"])
+    ap.add_argument("--tile", default=None, help="bx,by,bz")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2304_06437_gb300 import Solver
+
+    lattice, dims, tau = w["lattice"], w["dims"], w["tau"]
+    faces, wall_u = boundary(w)
+    N = dims[0] * dims[1] * dims[2]
+    stream = torch.cuda.Stream()
+    tile = tuple(int(v) for v in args.tile.split(",")) if args.tile else None
+    s = Solver(lattice, dims, tau, faces=faces, wall_u=wall_u, storage=args.storage, scheme=args.scheme,
+               stream=stream, tile=tile)
+    info = s.info()
+    init_state(s, w, torch)
+    for _ in range(args.warmup):
+        s.step(1)
+    s.sync()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # ---- device-resident timing: events around every launch on the solver's stream
+    clocks = ClockSampler(torch.cuda.current_device())
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev[0].record(stream)
+    for i in range(args.steps):
+        s.step(1)
+        ev[i + 1].record(stream)
+    s.sync()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    per_launch = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[args.steps])
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * N * args.steps / (total_ms * 1e-3) / 1e6
+    ms_per_step = total_ms / args.steps
+    launches_per_step = 1 if args.scheme == "fused" else 2
+
+    es = STORAGE_BYTES[args.storage]
+    q = Q[lattice]
+    alg_bytes = 2 * q * es * N  # one read + one write of every population
+    avg_launch_s = float(np.mean(per_launch)) * 1e-3
+    peak, peak_kind = read_peaks()
+    achieved = alg_bytes / avg_launch_s / 1e9
+    traffic_per_update = read_traffic("%s_%s_%s" % (args.scheme, lattice, args.storage))
+    roofline = {
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        "peak_kind": peak_kind,
+        "traffic": traffic_per_update * N if traffic_per_update else None,
+        "kernel": "k1_fused_step" if args.scheme == "fused" else "k0_moments+k0_rebuild",
+        "algorithmic_bytes_per_update": 2 * q * es,
+    }
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(s, w, args, torch, stream)
+
+    s.close()
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, cores, sample = cpu_oracle_rate(lattice)
+        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.storage == "f64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "lattice": lattice, "dims": list(dims), "tau": tau,
+                       "storage": args.storage, "scheme": args.scheme, "tile": list(info["tile"]),
+                       "flow": w["flow"], "l2_flush": "inputs larger than L2 (%.1f GB population array)" % (
+                           info["population_bytes"] / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": launches_per_step * args.steps,
+            "per_launch_ms": {"mean": float(np.mean(per_launch)), "min": float(np.min(per_launch)),
+                              "max": float(np.max(per_launch))},
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measure_e2e(s, w, args, torch, stream):
+    """Same metric through the public API with pinned host buffers: host
+    (rho, u) -> lb_init_moments -> K steps -> lb_moments -> host."""
+    dims = w["dims"]
+    N = dims[0] * dims[1] * dims[2]
+    d = 2 if w["lattice"] == "D2Q9" else 3
+    try:
+        rho_h = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        u_h = torch.empty((d, N), dtype=torch.float64, pin_memory=True)
+        rho_o = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        u_o = torch.empty((d, N), dtype=torch.float64, pin_memory=True)
+    except Exception as exc:  # host memory too small for the full workload
+        return {"value": None, "unit": "MLUPS", "error": "pinned allocation failed: %s" % str(exc)[:120]}
+    rho_h.fill_(1.0)
+    u_h.zero_()
+    rn, un, ro, uo = (t.numpy() for t in (rho_h, u_h, rho_o, u_o))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.init_moments(rn, un)
+    s.step(args.steps)
+    s.moments(ro, uo)
+    dt = time.perf_counter() - t0
+    h2d = (1 + d) * N * 8
+    return {"value": N * args.steps / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
+            "d2h_bytes_per_step": h2d / args.steps, "seconds": dt}
+
+
+if __name__ == "__main__":
+    main()

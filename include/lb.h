@@ -1,0 +1,192 @@
+/*
+ * lb.h -- C ABI of the GB300 thread-safe regularized lattice Boltzmann library.
+ *
+ * Method: "Thread-safe lattice Boltzmann for high-performance computing on
+ * GPUs" (arXiv 2304.06437).  One time step rebuilds every population from the
+ * hydrodynamic moments of its upstream node,
+ *     f_a(x, t+1) = f^eq_a(rho, u)(x - c_a) + (1 - omega) fhat^neq_a(Pi^neq)(x - c_a)
+ * (section 3, the multline step equation; fhat^neq is the order-2 Hermite
+ * projection of Eq. hermite; f^eq the He-Luo equilibrium of Eq. equil), with
+ * halfway bounce-back walls and a moving lid (section 5.1) fused in.  The
+ * state is ONE population array; no second array is allocated (section 4,
+ * memory discussion).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: LB_OK (0) or a negative LB_E_* code.  Nothing aborts, no
+ *    C++ exception crosses the ABI.  lb_status_string() names a code.
+ *  - Node index idx = x + nx*(y + ny*z) ("canonical"); in 2D (D2Q9) nz = 1.
+ *  - Population arrays are [q][N] doubles in the canonical velocity order:
+ *    rest first, then by |c|^2, then lexicographically on (cx, cy, cz) with
+ *    -1 < 0 < 1.  Velocity fields are [d][N]; a symmetric tensor is [3][N]
+ *    (xx, yy, xy) in 2D and [6][N] (xx, yy, zz, xy, xz, yz) in 3D.
+ *  - Faces are ordered -x, +x, -y, +y, -z, +z.  Opposite faces are either both
+ *    periodic or both non-periodic.  A wall sits half a link outside the
+ *    outermost node, so dims counts fluid nodes.
+ *  - "u" is the velocity the state reports, u = (sum_a f_a c_a + F/2) / rho0
+ *    (incompressible He-Luo reading of section 2 with a body force F).
+ *  - Pointers: arguments named *_host are host memory; with on_device != 0 a
+ *    pointer is device memory of the context's device, readable/writable on
+ *    the context's stream.  Caller-owned buffers are only accessed during the
+ *    call; the library owns everything it allocates and frees it in
+ *    lb_destroy().
+ *  - Streams: work is enqueued on the context stream (lb_options.stream, or a
+ *    non-blocking stream the library creates).  lb_step() returns once the
+ *    work is enqueued; calls that return data synchronise the stream first.
+ *  - Threads: a context is not internally locked; use one context per host
+ *    thread (or serialise calls).
+ */
+#ifndef LB_H
+#define LB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LB_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define LB_API __attribute__((visibility("default")))
+#else
+#define LB_API
+#endif
+
+/* status codes */
+#define LB_OK 0
+#define LB_E_INVAL (-1)       /* bad argument, unsupported combination of sizes or kinds */
+#define LB_E_NOMEM (-2)       /* device or host allocation failed */
+#define LB_E_CUDA (-3)        /* a CUDA runtime call failed (no device, launch error, ...) */
+#define LB_E_DIVERGED (-4)    /* a reduction found a non-finite value */
+#define LB_E_TIMEOUT (-5)     /* a kernel gave up waiting for an asynchronous copy */
+#define LB_E_UNSUPPORTED (-6) /* valid request this build does not implement */
+
+typedef enum { LB_D2Q9 = 0, LB_D3Q19 = 1, LB_D3Q27 = 2 } lb_lattice;
+typedef enum { LB_PERIODIC = 0, LB_WALL = 1, LB_MOVING_WALL = 2 } lb_face_kind;
+
+/* Storage precision of the population array.  Every mode stores the shifted
+ * population f_a - t_a rho0 (exact in FP64; the accurate representation in the
+ * narrower formats); arithmetic is FP64 for LB_F64 and FP32 otherwise. */
+typedef enum { LB_F64 = 0, LB_F32 = 1, LB_F16S = 2, LB_BF16S = 3 } lb_storage;
+
+/* Kernel schedule.
+ *  LB_SCHEME_FUSED    one fused pull-stream + regularized-collision launch per
+ *                     step over brick columns; neighbouring bricks exchange
+ *                     post-collision boundary populations through a small
+ *                     double-buffered shell (the default, the fast path).
+ *  LB_SCHEME_TWO_PASS the paper's own schedule (section 4): a moments kernel
+ *                     writes rho, u, Pi^neq to full-size arrays, then a rebuild
+ *                     kernel pulls them and writes the populations. */
+typedef enum { LB_SCHEME_FUSED = 0, LB_SCHEME_TWO_PASS = 1 } lb_scheme;
+
+typedef struct {
+  int32_t kind[6];      /* lb_face_kind per face */
+  double wall_u[6][3];  /* wall velocity per face, read for LB_MOVING_WALL */
+} lb_boundary;
+
+typedef struct {
+  int32_t storage;      /* lb_storage; default LB_F32 */
+  int32_t scheme;       /* lb_scheme; default LB_SCHEME_FUSED */
+  double rho0;          /* reference density; default 1 */
+  double force[3];      /* body force per unit volume, lattice units; default 0 */
+  void* stream;         /* cudaStream_t to enqueue on; NULL = library-owned stream */
+  int32_t tile[3];      /* fused scheme: brick cross-section (bx, by) and sweep
+                           length bz; 0 = library choice */
+  int32_t device;       /* CUDA device ordinal; -1 = the current device */
+} lb_options;
+
+typedef struct lb_ctx lb_ctx;
+
+typedef struct {
+  int32_t lattice, q, d, storage, scheme;
+  int64_t dims[3];
+  int64_t steps_done;
+  int32_t tile[3];          /* brick (bx, by, bz) used by the fused scheme */
+  uint64_t population_bytes; /* the one population array */
+  uint64_t aux_bytes;        /* shells (fused) or moment arrays (two-pass) */
+  uint64_t algorithmic_bytes_per_update; /* 2 q s: one read + one write per population */
+} lb_info_t;
+
+/* Fills *opt with the defaults listed above. */
+LB_API void lb_default_options(lb_options* opt);
+
+/* Creates a context: allocates the population array (and the shell or moment
+ * buffers of the chosen scheme) on the device and zeroes the state (rest at
+ * rho0).  dims[2] must be 1 for D2Q9.  tau > 1/2 (nu = (tau - 1/2)/3, section
+ * 2).  bnd may be NULL (all periodic); opt may be NULL (defaults).
+ * Errors: LB_E_INVAL for bad sizes/kinds, LB_E_NOMEM, LB_E_CUDA. */
+LB_API int lb_create(int32_t lattice, const int64_t dims[3], double tau, const lb_boundary* bnd,
+              const lb_options* opt, lb_ctx** out);
+
+/* Sets the state to f = f^eq(rho, u) + fhat^neq(pineq) - t_a c_a.F/(2 cs2):
+ * Eq. equil plus the order-2 Hermite non-equilibrium part, shifted so that
+ * the state reports u.  rho [N], u [d][N], pineq [3 or 6][N] or NULL (= 0).
+ * All three are host (on_device = 0) or device (on_device = 1) FP64 arrays. */
+LB_API int lb_init_moments(lb_ctx* ctx, const double* rho, const double* u, const double* pineq,
+                    int32_t on_device);
+
+/* Uniform equilibrium state (rho, u[0..d-1]); no caller buffers. */
+LB_API int lb_init_uniform(lb_ctx* ctx, double rho, const double u[3]);
+
+/* Copies populations in/out, [q][N] FP64, canonical order.  Setting rounds to
+ * the storage precision. */
+LB_API int lb_set_populations(lb_ctx* ctx, const double* f, int32_t on_device);
+LB_API int lb_get_populations(lb_ctx* ctx, double* f, int32_t on_device);
+
+/* Reads the populations of the box [lo, lo+size) into host memory f_host,
+ * laid out [q][size_z][size_y][size_x].  For sampled checks on large grids. */
+LB_API int lb_get_region(lb_ctx* ctx, const int64_t lo[3], const int64_t size[3], double* f_host);
+
+/* Enqueues n time steps on the context stream (asynchronous). */
+LB_API int lb_step(lb_ctx* ctx, int64_t n);
+
+/* Density rho [N] and velocity u [d][N] of the stored state (FP64 sums). */
+LB_API int lb_moments(lb_ctx* ctx, double* rho, double* u, int32_t on_device);
+
+/* FP64 on-device reductions over all nodes: total mass sum rho, total momentum
+ * sum_a f_a c_a (without the F/2 shift), and -- if residual is not NULL -- the
+ * relative velocity change ||u - u_prev||_2 / ||u||_2 since the previous call
+ * that asked for it (1.0 on the first such call).  Deterministic (fixed
+ * reduction order).  Returns LB_E_DIVERGED if a value is not finite. */
+LB_API int lb_reduce(lb_ctx* ctx, double* mass, double mom[3], double* residual);
+
+/* Waits for the context stream; reports a sticky kernel status (LB_E_TIMEOUT). */
+LB_API int lb_sync(lb_ctx* ctx);
+
+/* Frees everything the context owns.  NULL is allowed. */
+LB_API void lb_destroy(lb_ctx* ctx);
+
+/* Describes a context (sizes, scheme, bytes). */
+LB_API int lb_info(const lb_ctx* ctx, lb_info_t* info);
+
+/* Host-only: the velocity table of a lattice in canonical order, c [q][3]
+ * (cz = 0 in 2D), weights w [q], opposite index opp [q].  Returns q or
+ * LB_E_INVAL.  Needs no GPU. */
+LB_API int lb_lattice_table(int32_t lattice, int32_t* c, double* w, int32_t* opp);
+
+/* Host-only memory accounting (section 4 of the paper): the number of
+ * full-size arrays and bytes per node each schedule keeps for a lattice --
+ * the paper's moment scheme (q + m arrays), a two-array "flip-flop" scheme
+ * (2q + d + 1 arrays) and this library's fused single-array scheme (q arrays
+ * plus the shell, reported separately by lb_info).  s = bytes per value.
+ * Needs no GPU. */
+typedef struct {
+  int32_t q, m;                 /* populations, stored moments 1 + d + d(d+1)/2 */
+  int32_t arrays_moment_scheme; /* q + m      (15 for D2Q9, 29 for D3Q19) */
+  int32_t arrays_flip_flop;     /* 2q + d + 1 (21 for D2Q9, 42 for D3Q19) */
+  int32_t arrays_single;        /* q */
+  double bytes_per_node_moment_scheme, bytes_per_node_flip_flop, bytes_per_node_single;
+} lb_memory_plan_t;
+LB_API int lb_memory_plan(int32_t lattice, int32_t bytes_per_value, lb_memory_plan_t* out);
+
+/* Human-readable name of a status code. */
+LB_API const char* lb_status_string(int code);
+
+/* ABI version of the loaded library (LB_ABI_VERSION it was built with). */
+LB_API int lb_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LB_H */

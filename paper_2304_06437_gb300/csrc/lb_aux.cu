@@ -1,0 +1,371 @@
+// lb_aux.cu -- state conversion, readout and FP64 reductions.
+//
+// These kernels move data between the caller's canonical FP64 arrays and the
+// internal shifted population array ft_a = f_a - t_a rho0 (row pitch padded to
+// a multiple of 32 elements), and compute the diagnostics of the ABI.  Every
+// node is handled by one thread; 64-bit indices throughout.
+#include <cuda_runtime.h>
+
+#include "lb_dispatch.cuh"
+
+namespace lbgb {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRedBlocks = 1024;  // fixed: the reduction order never depends on the GPU
+
+struct Layout {
+  int nx;          // internal x extent (= user x extent)
+  int64_t rows;    // ny * nz internal rows
+  int64_t pitch;
+  int64_t vol;
+  int64_t n;       // nx * rows
+};
+
+inline Layout layout_of(const Geometry& g) {
+  Layout l;
+  l.nx = g.nx;
+  l.rows = static_cast<int64_t>(g.ny) * g.nz;
+  l.pitch = g.pitch;
+  l.vol = g.vol;
+  l.n = static_cast<int64_t>(g.nx) * l.rows;
+  return l;
+}
+
+__device__ __forceinline__ int64_t ioff(const Layout& l, int64_t idx) {
+  const int64_t x = idx % l.nx;
+  const int64_t r = idx / l.nx;
+  return x + r * l.pitch;
+}
+
+// user vector component k -> internal axis
+template <class L>
+__device__ __forceinline__ constexpr int user_axis(int k) {
+  return (L::D == 2 && k == 1) ? 2 : k;
+}
+
+template <class L, class S, class R>
+__global__ void set_pop_kernel(Layout l, const double* __restrict__ f, S* __restrict__ ft, double rho0) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < l.n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = ioff(l, idx);
+    static_for<0, L::Q>([&](auto A_) {
+      constexpr int a = decltype(A_)::value;
+      const double v = f[a * l.n + idx] - weight<L>(a) * rho0;
+      ft[a * l.vol + o] = store_as<S, R>(static_cast<R>(v));
+    });
+  }
+}
+
+template <class L, class S, class R>
+__global__ void get_pop_kernel(Layout l, const S* __restrict__ ft, double* __restrict__ f, double rho0) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < l.n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = ioff(l, idx);
+    static_for<0, L::Q>([&](auto A_) {
+      constexpr int a = decltype(A_)::value;
+      f[a * l.n + idx] = static_cast<double>(load_as<S, R>(ft[a * l.vol + o])) + weight<L>(a) * rho0;
+    });
+  }
+}
+
+// f = f^eq(rho, u) + t_a (cc - cs2 I):Pi/(2 cs2^2) - t_a c.F/(2 cs2), in FP64,
+// stored shifted.  rho may be null (uniform rho_u), u may be null (uniform u_u).
+template <class L, class S, class R>
+__global__ void init_kernel(Layout l, S* __restrict__ ft, double rho0, const double* __restrict__ rho,
+                            const double* __restrict__ u, const double* __restrict__ pineq, double rho_u,
+                            double ux_u, double uy_u, double uz_u, double Fx, double Fy, double Fz) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < l.n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = ioff(l, idx);
+    const double r = rho ? rho[idx] : rho_u;
+    double ui[3] = {0.0, 0.0, 0.0};
+    const double uu[3] = {ux_u, uy_u, uz_u};
+    for (int k = 0; k < L::D; ++k) ui[user_axis<L>(k)] = u ? u[k * l.n + idx] : uu[k];
+    double P[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    if (pineq) {
+      if (L::D == 2) {
+        P[0][0] = pineq[0 * l.n + idx];
+        P[2][2] = pineq[1 * l.n + idx];
+        P[0][2] = P[2][0] = pineq[2 * l.n + idx];
+      } else {
+        P[0][0] = pineq[0 * l.n + idx];
+        P[1][1] = pineq[1 * l.n + idx];
+        P[2][2] = pineq[2 * l.n + idx];
+        P[0][1] = P[1][0] = pineq[3 * l.n + idx];
+        P[0][2] = P[2][0] = pineq[4 * l.n + idx];
+        P[1][2] = P[2][1] = pineq[5 * l.n + idx];
+      }
+    }
+    const double Fi[3] = {Fx, Fy, Fz};
+    const double drho = r - rho0;
+    double usq = 0.0, trP = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      usq += ui[k] * ui[k];
+      trP += P[k][k];
+    }
+    static_for<0, L::Q>([&](auto A_) {
+      constexpr int a = decltype(A_)::value;
+      constexpr int c[3] = {L::cx(a), L::cy(a), L::cz(a)};
+      double cu = 0.0, cF = 0.0, cPc = 0.0;
+      for (int i = 0; i < 3; ++i) {
+        cu += c[i] * ui[i];
+        cF += c[i] * Fi[i];
+        for (int j = 0; j < 3; ++j) cPc += c[i] * c[j] * P[i][j];
+      }
+      const double w = weight<L>(a);
+      const double v = w * (drho + rho0 * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq)) +
+                       w * 4.5 * (cPc - trP / 3.0) - w * 1.5 * cF;
+      ft[a * l.vol + o] = store_as<S, R>(static_cast<R>(v));
+    });
+  }
+}
+
+template <class L, class S, class R>
+__global__ void moments_kernel(Layout l, const S* __restrict__ ft, double rho0, double Fx, double Fy, double Fz,
+                               double* __restrict__ rho, double* __restrict__ u) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < l.n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = ioff(l, idx);
+    double dr = 0.0, j[3] = {0.0, 0.0, 0.0};
+    static_for<0, L::Q>([&](auto A_) {
+      constexpr int a = decltype(A_)::value;
+      const double v = static_cast<double>(load_as<S, R>(ft[a * l.vol + o]));
+      constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+      dr += v;
+      j[0] += cx * v;
+      j[1] += cy * v;
+      j[2] += cz * v;
+    });
+    if (rho) rho[idx] = rho0 + dr;
+    if (u) {
+      const double Fi[3] = {Fx, Fy, Fz};
+      for (int k = 0; k < L::D; ++k) {
+        const int ax = user_axis<L>(k);
+        u[k * l.n + idx] = (j[ax] + 0.5 * Fi[ax]) / rho0;
+      }
+    }
+  }
+}
+
+// region [lo, lo + size) in internal coordinates -> out [q][sz][sy][sx]
+template <class L, class S, class R>
+__global__ void region_kernel(Layout l, int ny, const S* __restrict__ ft, double rho0, int64_t x0, int64_t y0,
+                              int64_t z0, int64_t sx, int64_t sy, int64_t sz, double* __restrict__ out) {
+  const int64_t n = sx * sy * sz;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = x0 + i % sx;
+    const int64_t y = y0 + (i / sx) % sy;
+    const int64_t z = z0 + i / (sx * sy);
+    const int64_t o = x + l.pitch * (y + (int64_t)ny * z);
+    static_for<0, L::Q>([&](auto A_) {
+      constexpr int a = decltype(A_)::value;
+      out[a * n + i] = static_cast<double>(load_as<S, R>(ft[a * l.vol + o])) + weight<L>(a) * rho0;
+    });
+  }
+}
+
+// Per-block FP64 partials: [mass, jx, jy, jz, sum |u - u_prev|^2, sum |u|^2,
+// non-finite count]; u in internal axes.  Fixed grid + tree order.
+constexpr int kRedFields = 7;
+
+template <class L, class S, class R>
+__global__ void __launch_bounds__(kThreads) reduce_kernel(Layout l, const S* __restrict__ ft, double rho0,
+                                                          double Fx, double Fy, double Fz,
+                                                          float* __restrict__ uprev, int residual,
+                                                          double* __restrict__ partial) {
+  double acc[kRedFields] = {0, 0, 0, 0, 0, 0, 0};
+  const double Fi[3] = {Fx, Fy, Fz};
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < l.n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = ioff(l, idx);
+    double dr = 0.0, j[3] = {0.0, 0.0, 0.0};
+    bool bad = false;
+    static_for<0, L::Q>([&](auto A_) {
+      constexpr int a = decltype(A_)::value;
+      const double v = static_cast<double>(load_as<S, R>(ft[a * l.vol + o]));
+      bad |= !isfinite(v);
+      constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+      dr += v;
+      j[0] += cx * v;
+      j[1] += cy * v;
+      j[2] += cz * v;
+    });
+    acc[0] += rho0 + dr;
+    acc[1] += j[0];
+    acc[2] += j[1];
+    acc[3] += j[2];
+    acc[6] += bad ? 1.0 : 0.0;
+    if (residual) {
+      for (int k = 0; k < 3; ++k) {
+        const double uk = (j[k] + 0.5 * Fi[k]) / rho0;
+        const double prev = static_cast<double>(uprev[k * l.n + idx]);
+        acc[4] += (uk - prev) * (uk - prev);
+        acc[5] += uk * uk;
+        uprev[k * l.n + idx] = static_cast<float>(uk);
+      }
+    }
+  }
+  __shared__ double sh[kRedFields][kThreads];
+  for (int k = 0; k < kRedFields; ++k) sh[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int k = 0; k < kRedFields; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kRedFields; ++k) partial[k * kRedBlocks + blockIdx.x] = sh[k][0];
+}
+
+__global__ void reduce_final_kernel(double* __restrict__ partial, int nblocks) {
+  // one block: fixed-order tree over the block partials
+  __shared__ double sh[kThreads];
+  for (int k = 0; k < kRedFields; ++k) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) a += partial[k * kRedBlocks + i];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[kRedFields * kRedBlocks + k] = sh[0];
+    __syncthreads();
+  }
+}
+
+int grid_for(int64_t n) {
+  int64_t b = (n + kThreads - 1) / kThreads;
+  if (b > 152 * 64) b = 152 * 64;
+  if (b < 1) b = 1;
+  return static_cast<int>(b);
+}
+
+}  // namespace
+
+cudaError_t aux_set_populations(lb_ctx* ctx, const double* f_dev) {
+  const Layout l = layout_of(ctx->g);
+  dispatch_lattice(ctx->lattice, [&](auto Lt) {
+    using L = decltype(Lt);
+    dispatch_storage(ctx->storage, [&](auto St, auto Rt) {
+      using S = typename decltype(St)::type;
+      using R = typename decltype(Rt)::type;
+      set_pop_kernel<L, S, R><<<grid_for(l.n), kThreads, 0, ctx->stream>>>(l, f_dev, static_cast<S*>(ctx->f),
+                                                                           ctx->g.rho0);
+    });
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t aux_get_populations(lb_ctx* ctx, double* f_dev) {
+  const Layout l = layout_of(ctx->g);
+  dispatch_lattice(ctx->lattice, [&](auto Lt) {
+    using L = decltype(Lt);
+    dispatch_storage(ctx->storage, [&](auto St, auto Rt) {
+      using S = typename decltype(St)::type;
+      using R = typename decltype(Rt)::type;
+      get_pop_kernel<L, S, R><<<grid_for(l.n), kThreads, 0, ctx->stream>>>(
+          l, static_cast<const S*>(ctx->f), f_dev, ctx->g.rho0);
+    });
+  });
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_init(lb_ctx* ctx, const double* rho, const double* u, const double* pineq, double rho_u,
+                               const double uu[3]) {
+  const Layout l = layout_of(ctx->g);
+  // the force is applied in internal axes inside the kernel
+  const double* F = ctx->g.force;
+  dispatch_lattice(ctx->lattice, [&](auto Lt) {
+    using L = decltype(Lt);
+    dispatch_storage(ctx->storage, [&](auto St, auto Rt) {
+      using S = typename decltype(St)::type;
+      using R = typename decltype(Rt)::type;
+      init_kernel<L, S, R><<<grid_for(l.n), kThreads, 0, ctx->stream>>>(
+          l, static_cast<S*>(ctx->f), ctx->g.rho0, rho, u, pineq, rho_u, uu[0], uu[1], uu[2], F[0], F[1], F[2]);
+    });
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t aux_init_moments(lb_ctx* ctx, const double* rho, const double* u, const double* pineq) {
+  const double zero[3] = {0, 0, 0};
+  return launch_init(ctx, rho, u, pineq, ctx->g.rho0, zero);
+}
+
+cudaError_t aux_init_uniform(lb_ctx* ctx, double rho, const double u_user[3]) {
+  return launch_init(ctx, nullptr, nullptr, nullptr, rho, u_user);
+}
+
+cudaError_t aux_moments(lb_ctx* ctx, double* rho, double* u) {
+  const Layout l = layout_of(ctx->g);
+  const double* F = ctx->g.force;
+  dispatch_lattice(ctx->lattice, [&](auto Lt) {
+    using L = decltype(Lt);
+    dispatch_storage(ctx->storage, [&](auto St, auto Rt) {
+      using S = typename decltype(St)::type;
+      using R = typename decltype(Rt)::type;
+      moments_kernel<L, S, R><<<grid_for(l.n), kThreads, 0, ctx->stream>>>(
+          l, static_cast<const S*>(ctx->f), ctx->g.rho0, F[0], F[1], F[2], rho, u);
+    });
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t aux_get_region(lb_ctx* ctx, const int64_t lo[3], const int64_t size[3], double* f_dev) {
+  const Layout l = layout_of(ctx->g);
+  // user box -> internal box (2D: user y is internal z)
+  int64_t x0 = lo[0], y0 = lo[1], z0 = lo[2], sx = size[0], sy = size[1], sz = size[2];
+  if (ctx->g.d == 2) {
+    z0 = lo[1];
+    sz = size[1];
+    y0 = 0;
+    sy = 1;
+  }
+  const int64_t n = sx * sy * sz;
+  const int ny = ctx->g.ny;
+  dispatch_lattice(ctx->lattice, [&](auto Lt) {
+    using L = decltype(Lt);
+    dispatch_storage(ctx->storage, [&](auto St, auto Rt) {
+      using S = typename decltype(St)::type;
+      using R = typename decltype(Rt)::type;
+      region_kernel<L, S, R><<<grid_for(n), kThreads, 0, ctx->stream>>>(
+          l, ny, static_cast<const S*>(ctx->f), ctx->g.rho0, x0, y0, z0, sx, sy, sz, f_dev);
+    });
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t aux_reduce(lb_ctx* ctx, double* host_out, bool residual) {
+  const Layout l = layout_of(ctx->g);
+  const double* F = ctx->g.force;
+  cudaError_t err = cudaSuccess;
+  if (residual && !ctx->d_uprev) {
+    err = cudaMallocAsync(reinterpret_cast<void**>(&ctx->d_uprev), sizeof(float) * 3 * l.n, ctx->stream);
+    if (err != cudaSuccess) return err;
+    err = cudaMemsetAsync(ctx->d_uprev, 0, sizeof(float) * 3 * l.n, ctx->stream);
+    if (err != cudaSuccess) return err;
+  }
+  dispatch_lattice(ctx->lattice, [&](auto Lt) {
+    using L = decltype(Lt);
+    dispatch_storage(ctx->storage, [&](auto St, auto Rt) {
+      using S = typename decltype(St)::type;
+      using R = typename decltype(Rt)::type;
+      reduce_kernel<L, S, R><<<kRedBlocks, kThreads, 0, ctx->stream>>>(
+          l, static_cast<const S*>(ctx->f), ctx->g.rho0, F[0], F[1], F[2], ctx->d_uprev, residual ? 1 : 0,
+          ctx->d_red);
+    });
+  });
+  reduce_final_kernel<<<1, kThreads, 0, ctx->stream>>>(ctx->d_red, kRedBlocks);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  err = cudaMemcpyAsync(host_out, ctx->d_red + kRedFields * kRedBlocks, sizeof(double) * kRedFields,
+                        cudaMemcpyDeviceToHost, ctx->stream);
+  if (err != cudaSuccess) return err;
+  return cudaStreamSynchronize(ctx->stream);
+}
+
+size_t reduce_scratch_doubles() { return static_cast<size_t>(kRedFields) * (kRedBlocks + 1); }
+
+}  // namespace lbgb

@@ -1,0 +1,261 @@
+// lb_collide.cuh -- the per-node arithmetic of the regularized step, shared by
+// every kernel so that all schedules produce bit-identical populations.
+//
+// All quantities are deviations: the stored population is ft_a = f_a - t_a rho0
+// and the density is drho = rho - rho0.  With cs^2 = 1/3:
+//
+//   moments (section 4, moment reconstruction):
+//     drho = sum ft_a,  j = sum ft_a c_a,  P = sum ft_a c_a c_a
+//     u = (j + F/2) / rho0                       (He-Luo reading, forcing shift)
+//     Pi^neq = P - drho cs2 I - rho0 u u          (= sum (f - f^eq) c c)
+//   post-collision set (Eq. LBexp with f^neq -> fhat^neq of Eq. hermite, plus
+//   the second-order forcing term):
+//     ft*_a = t_a [ A + B.c_a + c_a.C.c_a ]
+//     A = drho - 3/2 rho0 u.u - 3/2 (1-omega) tr Pi^neq - 3 (1 - omega/2) u.F
+//     B = 3 rho0 u + 3/2 F
+//     C = 9/2 [ rho0 u u + (1-omega) Pi^neq + (1 - omega/2)(u F + F u) ]
+//   This is t_a [drho + rho0 (c.u/cs2 + (cc - cs2 I):uu/(2 cs2^2))]
+//   + (1-omega) t_a [c.j^neq/cs2 + (cc - cs2 I):Pi^neq/(2 cs2^2)] + S_a with
+//   j^neq = -F/2, written as a quadratic form in c_a.
+//
+// Every operation is written out explicitly and the library is compiled with
+// -fmad=false, so the rounding sequence is fixed by this source: the fused
+// kernel, the two-pass kernel and the shell exporter evaluate the same
+// instructions on the same inputs and agree bit for bit.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include <type_traits>
+#include <utility>
+
+#include "lb_lattice.cuh"
+
+#define LB_DEV __device__ __forceinline__
+
+namespace lbgb {
+
+// compile-time loop: f(std::integral_constant<int, I>) for I in [B, E)
+template <int B, int E, class F>
+LB_DEV void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(std::forward<F>(f));
+  }
+}
+
+// ------------------------------------------------------------ storage types
+template <class S, class R> LB_DEV R load_as(const S v);
+template <> LB_DEV float load_as<float, float>(const float v) { return v; }
+template <> LB_DEV double load_as<double, double>(const double v) { return v; }
+template <> LB_DEV float load_as<__half, float>(const __half v) { return __half2float(v); }
+template <> LB_DEV float load_as<__nv_bfloat16, float>(const __nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <class S, class R> LB_DEV S store_as(const R v);
+template <> LB_DEV float store_as<float, float>(const float v) { return v; }
+template <> LB_DEV double store_as<double, double>(const double v) { return v; }
+template <> LB_DEV __half store_as<__half, float>(const float v) { return __float2half_rn(v); }
+template <> LB_DEV __nv_bfloat16 store_as<__nv_bfloat16, float>(const float v) { return __float2bfloat16_rn(v); }
+
+// round a value to the storage precision and back (identity for FP32/FP64)
+template <class S, class R>
+LB_DEV R round_to_storage(const R v) {
+  return load_as<S, R>(store_as<S, R>(v));
+}
+
+// ------------------------------------------------------------ parameters
+template <class R>
+struct Phys {
+  R rho0, inv_rho0;
+  R om1;     // 1 - omega
+  R g;       // 1 - omega / 2
+  R F[3];    // body force (internal axes)
+  R hF[3];   // F / 2
+  R cs2;     // 1/3 rounded to R
+};
+
+template <class R>
+struct Mom {
+  R drho;
+  R u[3];
+  R pi[6];  // Pi^neq: xx, yy, zz, xy, xz, yz (internal axes)
+};
+
+template <class R>
+struct Coef {
+  R A;
+  R B[3];
+  R C[3];   // diagonal xx, yy, zz
+  R C2[3];  // doubled off-diagonal: xy, xz, yz
+};
+
+// pair index helpers: the unordered pairs {a, opp(a)} with a < opp(a)
+template <class L>
+LB_HD constexpr int n_pairs() { return (L::Q - 1) / 2; }
+template <class L>
+LB_HD constexpr int pair_first(int p) {
+  int n = 0;
+  for (int a = 1; a < L::Q; ++a)
+    if (a < L::opp(a)) {
+      if (n == p) return a;
+      ++n;
+    }
+  return -1;
+}
+
+// off-diagonal slot of an axis pair (0,1)->0, (0,2)->1, (1,2)->2
+LB_HD constexpr int od(int al, int be) { return al + be - 1; }
+
+// ------------------------------------------------------------ moments
+template <class L, class R, bool FORCE>
+LB_DEV void moments(const R (&f)[L::Q], const Phys<R>& ph, Mom<R>& m) {
+  // even and odd pair sums: s = f_a + f_abar, t = f_a - f_abar
+  R s[n_pairs<L>()], t[n_pairs<L>()];
+  static_for<0, n_pairs<L>()>([&](auto P) {
+    constexpr int p = decltype(P)::value;
+    constexpr int a = pair_first<L>(p);
+    constexpr int b = L::opp(a);
+    s[p] = f[a] + f[b];
+    t[p] = f[a] - f[b];
+  });
+  R drho = f[0];
+  static_for<0, n_pairs<L>()>([&](auto P) { drho = drho + s[decltype(P)::value]; });
+  R j[3] = {R(0), R(0), R(0)};
+  R Pd[3] = {R(0), R(0), R(0)};
+  R Po[3] = {R(0), R(0), R(0)};
+  static_for<0, n_pairs<L>()>([&](auto P) {
+    constexpr int p = decltype(P)::value;
+    static_for<0, 3>([&](auto AL) {
+      constexpr int al = decltype(AL)::value;
+      constexpr int ca = comp<L>(al, pair_first<L>(p));
+      if constexpr (ca == 1) j[al] = j[al] + t[p];
+      if constexpr (ca == -1) j[al] = j[al] - t[p];
+      if constexpr (ca != 0) Pd[al] = Pd[al] + s[p];
+    });
+    static_for<0, 3>([&](auto AL) {
+      constexpr int al = decltype(AL)::value;
+      static_for<al + 1, 3>([&](auto BE) {
+        constexpr int be = decltype(BE)::value;
+        constexpr int cc = comp<L>(al, pair_first<L>(p)) * comp<L>(be, pair_first<L>(p));
+        if constexpr (cc == 1) Po[od(al, be)] = Po[od(al, be)] + s[p];
+        if constexpr (cc == -1) Po[od(al, be)] = Po[od(al, be)] - s[p];
+      });
+    });
+  });
+  m.drho = drho;
+  R ru[3];
+  static_for<0, 3>([&](auto AL) {
+    constexpr int al = decltype(AL)::value;
+    if constexpr (L::axis(al)) {
+      if constexpr (FORCE) m.u[al] = (j[al] + ph.hF[al]) * ph.inv_rho0;
+      else m.u[al] = j[al] * ph.inv_rho0;
+    } else {
+      m.u[al] = R(0);
+    }
+    ru[al] = ph.rho0 * m.u[al];
+  });
+  const R dcs = drho * ph.cs2;
+  static_for<0, 3>([&](auto AL) {
+    constexpr int al = decltype(AL)::value;
+    if constexpr (L::axis(al)) m.pi[al] = (Pd[al] - dcs) - ru[al] * m.u[al];
+    else m.pi[al] = R(0);
+  });
+  static_for<0, 3>([&](auto AL) {
+    constexpr int al = decltype(AL)::value;
+    static_for<al + 1, 3>([&](auto BE) {
+      constexpr int be = decltype(BE)::value;
+      if constexpr (L::axis(al) && L::axis(be)) m.pi[3 + od(al, be)] = Po[od(al, be)] - ru[al] * m.u[be];
+      else m.pi[3 + od(al, be)] = R(0);
+    });
+  });
+}
+
+// ------------------------------------------------------------ coefficients
+template <class L, class R, bool FORCE>
+LB_DEV void coeffs(const Mom<R>& m, const Phys<R>& ph, Coef<R>& k) {
+  R usq = R(0), tr = R(0), uF = R(0);
+  static_for<0, 3>([&](auto AL) {
+    constexpr int al = decltype(AL)::value;
+    if constexpr (L::axis(al)) {
+      usq = usq + m.u[al] * m.u[al];
+      tr = tr + m.pi[al];
+      if constexpr (FORCE) uF = uF + m.u[al] * ph.F[al];
+    }
+  });
+  R A = (m.drho - R(1.5) * (ph.rho0 * usq)) - R(1.5) * (ph.om1 * tr);
+  if constexpr (FORCE) A = A - R(3) * (ph.g * uF);
+  k.A = A;
+  static_for<0, 3>([&](auto AL) {
+    constexpr int al = decltype(AL)::value;
+    const R ru = ph.rho0 * m.u[al];
+    R b = R(3) * ru;
+    R c = ru * m.u[al] + ph.om1 * m.pi[al];
+    if constexpr (FORCE) {
+      b = b + R(1.5) * ph.F[al];
+      c = c + ph.g * (R(2) * (m.u[al] * ph.F[al]));
+    }
+    k.B[al] = b;
+    k.C[al] = R(4.5) * c;
+  });
+  static_for<0, 3>([&](auto AL) {
+    constexpr int al = decltype(AL)::value;
+    static_for<al + 1, 3>([&](auto BE) {
+      constexpr int be = decltype(BE)::value;
+      R c = (ph.rho0 * m.u[al]) * m.u[be] + ph.om1 * m.pi[3 + od(al, be)];
+      if constexpr (FORCE) c = c + ph.g * (m.u[al] * ph.F[be] + ph.F[al] * m.u[be]);
+      k.C2[od(al, be)] = R(9) * c;
+    });
+  });
+}
+
+// ------------------------------------------------------------ one population
+// ft*_a = t_a (even + odd), even = A + sum_{c_al != 0} C_alal + sum c_al c_be C2,
+// odd = sum c_al B_al
+template <class L, class R, int a>
+LB_DEV R post(const Coef<R>& k) {
+  R even = k.A;
+  static_for<0, 3>([&](auto AL) {
+    constexpr int al = decltype(AL)::value;
+    if constexpr (comp<L>(al, a) != 0) even = even + k.C[al];
+  });
+  static_for<0, 3>([&](auto AL) {
+    constexpr int al = decltype(AL)::value;
+    static_for<al + 1, 3>([&](auto BE) {
+      constexpr int be = decltype(BE)::value;
+      constexpr int cc = comp<L>(al, a) * comp<L>(be, a);
+      if constexpr (cc == 1) even = even + k.C2[od(al, be)];
+      if constexpr (cc == -1) even = even - k.C2[od(al, be)];
+    });
+  });
+  // odd part: the sum of the signed B components in axis order; for opp(a)
+  // every term is negated, so the result is exactly negated as well
+  R odd = R(0);
+  bool first = true;
+  static_for<0, 3>([&](auto AL) {
+    constexpr int al = decltype(AL)::value;
+    constexpr int ca = comp<L>(al, a);
+    if constexpr (ca != 0) {
+      const R term = (ca == 1) ? k.B[al] : -k.B[al];
+      odd = first ? term : odd + term;
+      first = false;
+    }
+  });
+  constexpr R w = R(weight<L>(a));
+  return w * (even + odd);
+}
+
+// full regularized collision of one node: ft -> ft*
+template <class L, class R, bool FORCE>
+LB_DEV void collide(const R (&f)[L::Q], const Phys<R>& ph, R (&out)[L::Q]) {
+  Mom<R> m;
+  moments<L, R, FORCE>(f, ph, m);
+  Coef<R> k;
+  coeffs<L, R, FORCE>(m, ph, k);
+  static_for<0, L::Q>([&](auto A_) {
+    constexpr int a = decltype(A_)::value;
+    out[a] = post<L, R, a>(k);
+  });
+}
+
+}  // namespace lbgb

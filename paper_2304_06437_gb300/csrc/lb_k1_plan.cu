@@ -1,0 +1,123 @@
+// lb_k1_plan.cu -- brick decomposition of the fused step: picks a compiled
+// brick shape, the sweep length bz, and lays out the shell buffers.
+#include <cstdio>
+
+#include "lb_k1_launch.cuh"
+
+namespace lbgb {
+
+extern const K1Variant k1_variants_d2q9[];
+extern const int k1_n_variants_d2q9;
+extern const K1Variant k1_variants_d3q19[];
+extern const int k1_n_variants_d3q19;
+extern const K1Variant k1_variants_d3q27[];
+extern const int k1_n_variants_d3q27;
+
+static const K1Variant* find_variant(int lattice, int storage, int bx, int by) {
+  const K1Variant* list = nullptr;
+  int n = 0;
+  switch (lattice) {
+    case LB_D2Q9: list = k1_variants_d2q9; n = k1_n_variants_d2q9; break;
+    case LB_D3Q19: list = k1_variants_d3q19; n = k1_n_variants_d3q19; break;
+    case LB_D3Q27: list = k1_variants_d3q27; n = k1_n_variants_d3q27; break;
+    default: return nullptr;
+  }
+  for (int i = 0; i < n; ++i) {
+    const K1Variant& v = list[i];
+    if (v.storage != storage) continue;
+    if (bx > 0 && v.bx != bx) continue;
+    if (by > 0 && v.by != by) continue;
+    return &v;
+  }
+  return nullptr;
+}
+
+static int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 152;
+  return n;
+}
+
+// Sweep length: bricks per wave fill the SMs evenly (one CTA per SM), while
+// each brick stays long enough that its pipeline fill/drain (about NS + 2
+// planes) and its z-shell traffic stay small.
+static int choose_bz(int nz, int columns, int slots, int sms) {
+  int best_bz = nz;
+  double best = -1.0;
+  for (int nbz = 1; nbz <= 64; ++nbz) {
+    const int bz = (nz + nbz - 1) / nbz;
+    if (bz < 8 && nbz > 1) break;
+    const int nbz_eff = (nz + bz - 1) / bz;
+    const double bricks = double(columns) * nbz_eff;
+    const double waves = bricks / sms;
+    const double fill = waves / std::ceil(waves);
+    const double pipe = double(bz) / double(bz + slots + 2);
+    const double score = fill * pipe;
+    if (score > best + 1e-9) {
+      best = score;
+      best_bz = bz;
+    }
+  }
+  return best_bz;
+}
+
+bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPlan* plan) {
+  const int rbx = tile_req ? tile_req[0] : 0;
+  const int rby = tile_req ? tile_req[1] : 0;
+  const K1Variant* v = find_variant(g.lattice, storage, rbx, rby);
+  if (!v) return false;
+  FusedPlan p{};
+  p.bx = v->bx;
+  p.by = v->by;
+  p.slots = v->ns;
+  p.smem_bytes = v->smem;
+  p.nbx = (g.nx + p.bx - 1) / p.bx;
+  p.nby = (g.ny + p.by - 1) / p.by;
+  const int columns = p.nbx * p.nby;
+  const int req_bz = tile_req ? tile_req[2] : 0;
+  p.bz = req_bz > 0 ? (req_bz < g.nz ? req_bz : g.nz) : choose_bz(g.nz, columns, p.slots, sm_count());
+  p.nbz = (g.nz + p.bz - 1) / p.bz;
+  int nxf = 0, nyf = 0, nzf = 0;
+  dispatch_lattice(g.lattice, [&](auto Lt) {
+    using L = decltype(Lt);
+    nxf = count_dirs<L>(0, 1);
+    nyf = count_dirs<L>(1, 1);
+    nzf = count_dirs<L>(2, 1);
+  });
+  p.nxf = nxf;
+  p.nyf = nyf;
+  p.nzf = nzf;
+  p.sx_elems = 2LL * p.nbx * nxf * int64_t(g.nz) * g.ny;
+  p.sy_elems = 2LL * p.nby * nyf * int64_t(g.nz) * g.nx;
+  p.sz_elems = 2LL * p.nbz * nzf * int64_t(g.ny) * g.nx;
+  p.parity_elems = ((p.sx_elems + p.sy_elems + p.sz_elems) + 31) / 32 * 32;
+  *plan = p;
+  return true;
+}
+
+static const K1Variant* ctx_variant(lb_ctx* ctx) {
+  return find_variant(ctx->lattice, ctx->storage, ctx->plan.bx, ctx->plan.by);
+}
+
+cudaError_t k1_configure(lb_ctx* ctx) {
+  const K1Variant* v = ctx_variant(ctx);
+  if (!v) return cudaErrorInvalidValue;
+  return v->configure();
+}
+
+cudaError_t k1_step(lb_ctx* ctx) {
+  const K1Variant* v = ctx_variant(ctx);
+  if (!v) return cudaErrorInvalidValue;
+  cudaError_t e = v->step(ctx);
+  if (e == cudaSuccess) ctx->parity = 1 - ctx->parity;
+  return e;
+}
+
+cudaError_t k1_bootstrap(lb_ctx* ctx) {
+  const K1Variant* v = ctx_variant(ctx);
+  if (!v) return cudaErrorInvalidValue;
+  return v->bootstrap(ctx);
+}
+
+}  // namespace lbgb

@@ -1,0 +1,192 @@
+"""Thin Python front end of the C ABI (include/lb.h).
+
+Only marshals arguments: every step of the method runs in the CUDA library.
+numpy arrays are passed as host buffers; torch CUDA tensors as device
+buffers (PyTorch provides device memory and streams, nothing else).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _binding as B
+
+
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+def _ptr(x, dtype=np.float64):
+    """(pointer, on_device) of a contiguous FP64 buffer."""
+    if x is None:
+        return None, 0
+    if _is_torch_cuda(x):
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise ValueError("device buffers must be contiguous torch.float64 tensors")
+        return ctypes.c_void_p(x.data_ptr()), 1
+    if not (isinstance(x, np.ndarray) and x.dtype == dtype and x.flags["C_CONTIGUOUS"]):
+        raise ValueError("host buffers must be C-contiguous float64 numpy arrays")
+    return ctypes.c_void_p(x.ctypes.data), 0
+
+
+class Solver:
+    """One lattice Boltzmann domain resident on the GPU.
+
+    lattice: "D2Q9" | "D3Q19" | "D3Q27"; dims: (nx, ny[, nz]); tau > 1/2;
+    faces: six face kinds (-x,+x,-y,+y,-z,+z) from {"periodic","wall",
+    "moving_wall"} or ints; wall_u: 6x3 wall velocities; storage: "f64" |
+    "f32" | "f16s" | "bf16s"; scheme: "fused" | "two_pass".
+    """
+
+    _FACE = {"periodic": B.LB_PERIODIC, "wall": B.LB_WALL, "moving_wall": B.LB_MOVING_WALL}
+
+    def __init__(self, lattice, dims, tau, faces=None, wall_u=None, storage="f32", scheme="fused",
+                 rho0=1.0, force=(0.0, 0.0, 0.0), stream=None, tile=None, device=-1):
+        self._lib = B.load()
+        self._ctx = ctypes.c_void_p()
+        self.lattice = lattice
+        self.lat_id = B.LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+        d = 2 if self.lat_id == B.LB_D2Q9 else 3
+        dims = list(dims) + [1] * (3 - len(dims))
+        self.dims = tuple(int(v) for v in dims[:3])
+        self.d = d
+        self.q = {0: 9, 1: 19, 2: 27}[self.lat_id]
+        self.n = self.dims[0] * self.dims[1] * self.dims[2]
+        bnd = B.lb_boundary()
+        faces = faces if faces is not None else [B.LB_PERIODIC] * 6
+        for k in range(6):
+            fk = faces[k] if k < len(faces) else B.LB_PERIODIC
+            bnd.kind[k] = self._FACE[fk] if isinstance(fk, str) else int(fk)
+            for al in range(3):
+                bnd.wall_u[k][al] = float(wall_u[k][al]) if wall_u is not None else 0.0
+        opt = B.lb_options()
+        self._lib.lb_default_options(ctypes.byref(opt))
+        opt.storage = B.STORAGES[storage] if isinstance(storage, str) else int(storage)
+        opt.scheme = B.SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+        opt.rho0 = float(rho0)
+        for k in range(3):
+            opt.force[k] = float(force[k]) if k < len(force) else 0.0
+        if stream is not None:
+            opt.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        if tile is not None:
+            for k in range(3):
+                opt.tile[k] = int(tile[k]) if k < len(tile) else 0
+        opt.device = int(device)
+        self.rho0 = float(rho0)
+        dims_arr = (ctypes.c_int64 * 3)(*self.dims)
+        B.check(self._lib.lb_create(self.lat_id, dims_arr, float(tau), ctypes.byref(bnd), ctypes.byref(opt),
+                                    ctypes.byref(self._ctx)), "lb_create")
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            self._lib.lb_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------ state
+    def init_moments(self, rho, u, pineq=None):
+        pr, dev = _ptr(rho)
+        pu, dev2 = _ptr(u)
+        pp, dev3 = _ptr(pineq)
+        if pineq is None:
+            dev3 = dev
+        if not (dev == dev2 == dev3):
+            raise ValueError("rho, u and pineq must all be host or all be device buffers")
+        B.check(self._lib.lb_init_moments(self._ctx, pr, pu, pp, dev), "lb_init_moments")
+
+    def init_uniform(self, rho, u=(0.0, 0.0, 0.0)):
+        uu = (ctypes.c_double * 3)(*(list(u) + [0.0] * 3)[:3])
+        B.check(self._lib.lb_init_uniform(self._ctx, float(rho), uu), "lb_init_uniform")
+
+    def set_populations(self, f):
+        p, dev = _ptr(f)
+        B.check(self._lib.lb_set_populations(self._ctx, p, dev), "lb_set_populations")
+
+    def get_populations(self, out=None):
+        out = np.empty((self.q, self.n)) if out is None else out
+        p, dev = _ptr(out)
+        B.check(self._lib.lb_get_populations(self._ctx, p, dev), "lb_get_populations")
+        return out
+
+    def get_region(self, lo, size):
+        lo3 = (list(lo) + [0, 0, 0])[:3]
+        sz3 = (list(size) + [1, 1, 1])[:3]
+        out = np.empty((self.q, sz3[0] * sz3[1] * sz3[2]))
+        B.check(self._lib.lb_get_region(self._ctx, (ctypes.c_int64 * 3)(*lo3), (ctypes.c_int64 * 3)(*sz3),
+                                        ctypes.c_void_p(out.ctypes.data)), "lb_get_region")
+        return out
+
+    # ------------------------------------------------------------ stepping
+    def step(self, n=1):
+        B.check(self._lib.lb_step(self._ctx, int(n)), "lb_step")
+
+    def sync(self):
+        B.check(self._lib.lb_sync(self._ctx), "lb_sync")
+
+    def moments(self, rho=None, u=None):
+        """Returns (rho [N], u [d][N]); pass torch CUDA tensors to stay on device."""
+        if rho is None and u is None:
+            rho = np.empty(self.n)
+            u = np.empty((self.d, self.n))
+        pr, dev = _ptr(rho)
+        pu, dev2 = _ptr(u)
+        if rho is not None and u is not None and dev != dev2:
+            raise ValueError("rho and u must both be host or both be device buffers")
+        B.check(self._lib.lb_moments(self._ctx, pr, pu, dev if rho is not None else dev2), "lb_moments")
+        return rho, u
+
+    def reduce(self, residual=False):
+        mass = ctypes.c_double()
+        mom = (ctypes.c_double * 3)()
+        res = ctypes.c_double()
+        rc = self._lib.lb_reduce(self._ctx, ctypes.byref(mass), mom, ctypes.byref(res) if residual else None)
+        B.check(rc, "lb_reduce")
+        out = {"mass": mass.value, "momentum": [mom[0], mom[1], mom[2]][: self.d]}
+        if residual:
+            out["residual"] = res.value
+        return out
+
+    def info(self) -> dict:
+        inf = B.lb_info_t()
+        B.check(self._lib.lb_info(self._ctx, ctypes.byref(inf)), "lb_info")
+        return {
+            "lattice": inf.lattice, "q": inf.q, "d": inf.d, "storage": inf.storage, "scheme": inf.scheme,
+            "dims": tuple(inf.dims), "steps_done": inf.steps_done, "tile": tuple(inf.tile),
+            "population_bytes": inf.population_bytes, "aux_bytes": inf.aux_bytes,
+            "algorithmic_bytes_per_update": inf.algorithmic_bytes_per_update,
+        }
+
+
+def lattice_table(lattice):
+    lib = B.load()
+    lid = B.LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+    q = {0: 9, 1: 19, 2: 27}[lid]
+    c = np.zeros((q, 3), dtype=np.int32)
+    w = np.zeros(q)
+    opp = np.zeros(q, dtype=np.int32)
+    B.check(lib.lb_lattice_table(lid, c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                 w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 opp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "lb_lattice_table")
+    return c, w, opp
+
+
+def memory_plan(lattice, bytes_per_value=4) -> dict:
+    lib = B.load()
+    lid = B.LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+    p = B.lb_memory_plan_t()
+    B.check(lib.lb_memory_plan(lid, int(bytes_per_value), ctypes.byref(p)), "lb_memory_plan")
+    return {name: getattr(p, name) for name, _ in p._fields_}

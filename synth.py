@@ -147,3 +147,38 @@ def smooth_random_state(dims, d: int, seed: int = SEED, du: float = 0.02, drho: 
 def uniform_noise(shape, seed: int = SEED) -> np.ndarray:
     """Raw U(-1, 1) numbers (e.g. to perturb populations beyond the Hermite span)."""
     return rng(seed).uniform(-1.0, 1.0, size=shape)
+
+
+# ------------------------------------------------------------------ on device
+# The same analytic fields generated with torch on the GPU, for grids too large
+# to build on the host (e.g. 512^3).  Same formulas as the numpy versions.
+def taylor_green_3d_torch(n: int, u0: float, rho0: float, tau: float, torch, device="cuda"):
+    k = 2.0 * math.pi / n
+    ar = torch.arange(n, device=device, dtype=torch.float64)
+    z, y, x = torch.meshgrid(ar, ar, ar, indexing="ij")
+    sx, cx = torch.sin(k * x), torch.cos(k * x)
+    sy, cy = torch.sin(k * y), torch.cos(k * y)
+    sz, cz = torch.sin(k * z), torch.cos(k * z)
+    u = torch.stack([u0 * sx * cy * cz, -u0 * cx * sy * cz, torch.zeros_like(x)]).reshape(3, -1)
+    p = rho0 * u0 * u0 / 16.0 * (torch.cos(2 * k * x) + torch.cos(2 * k * y)) * (torch.cos(2 * k * z) + 2.0)
+    rho = (rho0 + p / CS2).reshape(-1)
+    s = -rho0 * CS2 * tau
+    pineq = torch.stack([
+        s * 2 * (u0 * k * cx * cy * cz), s * 2 * (-u0 * k * cx * cy * cz), torch.zeros_like(x),
+        s * ((-u0 * k * sx * sy * cz) + (u0 * k * sx * sy * cz)), s * (-u0 * k * sx * cy * sz),
+        s * (u0 * k * cx * sy * sz),
+    ]).reshape(6, -1)
+    return rho.contiguous(), u.contiguous(), pineq.contiguous()
+
+
+def taylor_green_2d_torch(n: int, u0: float, rho0: float, tau: float, torch, device="cuda"):
+    k = 2.0 * math.pi / n
+    ar = torch.arange(n, device=device, dtype=torch.float64)
+    y, x = torch.meshgrid(ar, ar, indexing="ij")
+    u = torch.stack([-u0 * torch.cos(k * x) * torch.sin(k * y), u0 * torch.sin(k * x) * torch.cos(k * y)]).reshape(2, -1)
+    p = -rho0 * u0 * u0 / 4.0 * (torch.cos(2 * k * x) + torch.cos(2 * k * y))
+    rho = (rho0 + p / CS2).reshape(-1)
+    s = -rho0 * CS2 * tau
+    dudx = u0 * k * torch.sin(k * x) * torch.sin(k * y)
+    pineq = torch.stack([s * 2 * dudx, -s * 2 * dudx, torch.zeros_like(x)]).reshape(3, -1)
+    return rho.contiguous(), u.contiguous(), pineq.contiguous()

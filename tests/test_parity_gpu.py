@@ -1,0 +1,199 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (the benchmark spec): relative L2 on rho and u of 1e-12 in FP64 and 1e-5
+in FP32 storage/arithmetic; populations are also compared element by element.
+The fused single-array schedule must equal the paper's two-pass schedule bit
+for bit (same per-node arithmetic, lb_collide.cuh), and must not depend on the
+brick shape (a race would make it schedule dependent).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from lbcase import dim_of, faces_for, oracle_cfg, random_state, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+LATTICES = ["D2Q9", "D3Q19", "D3Q27"]
+TOL = {"f64": 1e-12, "f32": 1e-5}
+FTOL = {"f64": 1e-14, "f32": 2e-7}
+
+
+@pytest.fixture(scope="module")
+def Solver():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2304_06437_gb300 import build
+    build.build()
+    from paper_2304_06437_gb300 import Solver as S
+    return S
+
+
+def _dims(lat, kind="ragged"):
+    if dim_of(lat) == 2:
+        return {"ragged": (300, 37, 1), "tiny": (7, 5, 1)}[kind]
+    return {"ragged": (37, 21, 13), "tiny": (5, 4, 3)}[kind]
+
+
+def _run_pair(Solver, lat, dims, tau, fname, storage, scheme, steps, force=(0, 0, 0), tile=None, seed=101):
+    faces, wall_u = faces_for(lat, fname)
+    f0 = random_state(lat, dims, seed)
+    cfg = oracle_cfg(lat, dims, tau, faces, wall_u, force=force)
+    ref = oracle.run(cfg, f0, steps)
+    s = Solver(lat, dims, tau, faces=faces, wall_u=wall_u, storage=storage, scheme=scheme, force=force, tile=tile)
+    s.set_populations(np.ascontiguousarray(f0))
+    s.step(steps)
+    s.sync()
+    got = s.get_populations()
+    rho, u = s.moments()
+    s.close()
+    return ref, got, cfg, rho, u
+
+
+@pytest.mark.parametrize("lat", LATTICES)
+@pytest.mark.parametrize("fname", ["periodic", "walls", "lid", "duct", "lid_periodic_z"])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("scheme", ["fused", "two_pass"])
+def test_one_and_ten_steps_match_oracle(Solver, lat, fname, storage, scheme):
+    dims = _dims(lat)
+    force = (2e-5, 1e-5, 0.0) if fname == "duct" else (0, 0, 0)
+    # a short sweep length so that z-bricks and their shells are exercised
+    tile = None if scheme == "two_pass" else (0, 0, 5)
+    for steps in (1, 10):
+        ref, got, cfg, rho, u = _run_pair(Solver, lat, dims, 0.62, fname, storage, scheme, steps, force=force,
+                                          tile=tile)
+        assert np.abs(got - ref).max() < FTOL[storage] * 10 * steps, (steps, np.abs(got - ref).max())
+        r_ref, u_ref = oracle.moments(cfg, ref)
+        assert rel_l2(rho, r_ref) < TOL[storage]
+        assert rel_l2(u, u_ref) < TOL[storage], rel_l2(u, u_ref)
+
+
+@pytest.mark.parametrize("lat", LATTICES)
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("fname", ["lid", "periodic", "duct"])
+def test_fused_equals_two_pass_bitwise(Solver, lat, storage, fname):
+    dims = _dims(lat)
+    faces, wall_u = faces_for(lat, fname)
+    force = (2e-5, 0, 1e-5) if fname == "duct" else (0, 0, 0)
+    f0 = random_state(lat, dims, 7)
+    outs = []
+    for scheme, tile in (("two_pass", None), ("fused", None), ("fused", (0, 0, 4))):
+        s = Solver(lat, dims, 0.57, faces=faces, wall_u=wall_u, storage=storage, scheme=scheme, force=force,
+                   tile=tile)
+        s.set_populations(np.ascontiguousarray(f0))
+        s.step(12)
+        outs.append(s.get_populations())
+        s.close()
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[1], outs[2])
+
+
+@pytest.mark.parametrize("lat", ["D3Q19", "D3Q27"])
+def test_sweep_length_invariance(Solver, lat):
+    """Every brick split along z gives the same bits (a race would not)."""
+    dims = (40, 19, 23)
+    faces, wall_u = faces_for(lat, "lid_periodic_z")
+    f0 = random_state(lat, dims, 17)
+    outs = []
+    for bz in (0, 3, 8, 11, 23):
+        s = Solver(lat, dims, 0.55, faces=faces, wall_u=wall_u, storage="f32", tile=(0, 0, bz))
+        s.set_populations(np.ascontiguousarray(f0))
+        s.step(9)
+        outs.append(s.get_populations())
+        s.close()
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
+
+
+@pytest.mark.parametrize("lat", LATTICES)
+def test_degenerate_sizes(Solver, lat):
+    """Single-node-thick and smaller-than-a-brick grids, periodic and walled."""
+    cases = [(1, 1, 1), (1, 6, 1), (5, 1, 1)] if dim_of(lat) == 2 else [(1, 1, 1), (1, 9, 1), (3, 1, 7), (2, 2, 2)]
+    for dims in cases:
+        for fname in ("periodic", "walls"):
+            ref, got, cfg, rho, u = _run_pair(Solver, lat, dims, 0.9, fname, "f64", "fused", 3, seed=5)
+            assert np.abs(got - ref).max() < 1e-13, (dims, fname)
+
+
+def test_taylor_green_2d_fp64_and_fp32(Solver):
+    """Config: D2Q9 256^2 periodic Taylor-Green, u0 = 0.01, tau = 0.8, 1000 steps."""
+    n, tau, steps = 256, 0.8, 1000
+    rho, u, pineq = synth.taylor_green_2d(n, u0=0.01, tau=tau)
+    cfg = oracle.make_cfg("D2Q9", (n, n, 1), tau)
+    ref = oracle.run(cfg, oracle.init(cfg, rho, u, pineq), steps)
+    r_ref, u_ref = oracle.moments(cfg, ref)
+    for storage in ("f64", "f32"):
+        s = Solver("D2Q9", (n, n), tau, storage=storage)
+        s.init_moments(rho, np.ascontiguousarray(u), np.ascontiguousarray(pineq))
+        s.step(steps)
+        r, uu = s.moments()
+        s.close()
+        assert rel_l2(r, r_ref) < TOL[storage]
+        assert rel_l2(uu, u_ref) < TOL[storage], (storage, rel_l2(uu, u_ref))
+
+
+@pytest.mark.parametrize("lat,case", [("D3Q19", "cavity"), ("D3Q27", "tg")])
+def test_64cubed_configs(Solver, lat, case):
+    """Parity sizes of the 3D configs: D3Q19 lid-driven cavity (lid 0.05,
+    tau 0.52) and D3Q27 periodic Taylor-Green (u0 0.02, tau 0.8), 200 steps."""
+    n, steps = 64, 200
+    if case == "cavity":
+        tau = 0.52
+        faces, wall_u = faces_for(lat, "lid")
+        rho, u = synth.rest_state((n, n, n), 3)
+        pineq = None
+    else:
+        tau = 0.8
+        faces, wall_u = [0] * 6, None
+        rho, u, pineq = synth.taylor_green_3d(n, u0=0.02, tau=tau)
+    cfg = oracle.make_cfg(lat, (n, n, n), tau, faces=faces, wall_u=wall_u)
+    ref = oracle.run(cfg, oracle.init(cfg, rho, u, pineq), steps)
+    r_ref, u_ref = oracle.moments(cfg, ref)
+    for storage in ("f64", "f32"):
+        s = Solver(lat, (n, n, n), tau, faces=faces, wall_u=wall_u, storage=storage)
+        s.init_moments(rho, np.ascontiguousarray(u), None if pineq is None else np.ascontiguousarray(pineq))
+        s.step(steps)
+        r, uu = s.moments()
+        s.close()
+        assert rel_l2(r, r_ref) < TOL[storage]
+        assert rel_l2(uu, u_ref) < TOL[storage], (storage, rel_l2(uu, u_ref))
+
+
+@pytest.mark.parametrize("lat", LATTICES)
+def test_conservation_and_reductions(Solver, lat):
+    dims = (48, 40, 1) if dim_of(lat) == 2 else (24, 20, 18)
+    d = dim_of(lat)
+    rho, u, pineq = synth.smooth_random_state(dims, d, seed=3)
+    s = Solver(lat, dims, 0.56, storage="f64")
+    s.init_moments(rho, np.ascontiguousarray(u), np.ascontiguousarray(pineq))
+    r0 = s.reduce()
+    s.step(500)
+    r1 = s.reduce(residual=True)
+    s.close()
+    assert abs(r1["mass"] - r0["mass"]) / r0["mass"] < 1e-13
+    assert np.abs(np.array(r1["momentum"]) - np.array(r0["momentum"])).max() < 1e-13 * rho.size
+    assert abs(r0["mass"] - rho.sum()) < 1e-9
+    assert r1["residual"] == 1.0
+
+
+def test_init_moments_device_buffers_and_readback(Solver):
+    import torch
+    dims = (33, 17, 9)
+    rho, u, pineq = synth.smooth_random_state(dims, 3, seed=8)
+    s = Solver("D3Q19", dims, 0.7, storage="f64")
+    s.init_moments(torch.from_numpy(rho).cuda(), torch.from_numpy(np.ascontiguousarray(u)).cuda(),
+                   torch.from_numpy(np.ascontiguousarray(pineq)).cuda())
+    rt = torch.empty(rho.size, dtype=torch.float64, device="cuda")
+    ut = torch.empty((3, rho.size), dtype=torch.float64, device="cuda")
+    s.moments(rt, ut)
+    torch.cuda.synchronize()
+    assert np.abs(rt.cpu().numpy() - rho).max() < 1e-14
+    assert np.abs(ut.cpu().numpy() - u).max() < 1e-15
+    cfg = oracle.make_cfg("D3Q19", dims, 0.7)
+    fo = oracle.init(cfg, rho, u, pineq)
+    assert np.abs(s.get_populations() - fo).max() < 1e-15
+    box = s.get_region((3, 4, 5), (6, 2, 3))
+    full = s.get_populations().reshape(19, 9, 17, 33)
+    assert np.array_equal(box.reshape(19, 3, 2, 6), full[:, 5:8, 4:6, 3:9])
+    s.close()
