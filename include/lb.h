@@ -61,6 +61,7 @@ extern "C" {
 #define LB_E_DIVERGED (-4)    /* a reduction found a non-finite value */
 #define LB_E_TIMEOUT (-5)     /* a kernel gave up waiting for an asynchronous copy */
 #define LB_E_UNSUPPORTED (-6) /* valid request this build does not implement */
+#define LB_E_TOO_LARGE (-7)   /* grid exceeds the fixed scratch of lb_step_noalloc */
 
 typedef enum { LB_D2Q9 = 0, LB_D3Q19 = 1, LB_D3Q27 = 2 } lb_lattice;
 typedef enum { LB_PERIODIC = 0, LB_WALL = 1, LB_MOVING_WALL = 2 } lb_face_kind;
@@ -179,6 +180,32 @@ typedef struct {
   double bytes_per_node_moment_scheme, bytes_per_node_flip_flop, bytes_per_node_single;
 } lb_memory_plan_t;
 LB_API int lb_memory_plan(int32_t lattice, int32_t bytes_per_value, lb_memory_plan_t* out);
+
+/* Allocation-free step for callers that cannot let a library call
+ * cudaMalloc (device memory owned by another allocator or a fixed budget, or
+ * loops that must not enter the driver's allocator).  The paper has no
+ * counterpart: this is an interface variant of LB_SCHEME_TWO_PASS.
+ *
+ * Advances f by n steps in place, on `stream` (cudaStream_t, NULL = the
+ * default stream); returns once the work is enqueued.  f is the caller's
+ * device array of populations, [q][N] FP64 in the canonical order and layout
+ * of lb_set_populations(); the result equals lb_set_populations() +
+ * lb_step(n) + lb_get_populations() of an LB_F64 / LB_SCHEME_TWO_PASS
+ * context with the same arguments.  lattice, dims, tau, bnd (NULL = all
+ * periodic), rho0 and force (NULL = 0) mean what they mean for lb_create().
+ *
+ * Nothing is allocated: the moment arrays live in a file-scope device array
+ * of LB_NOALLOC_SCRATCH_BYTES, shared by every call on a device and kept
+ * until the process exits.  Hence (1 + d + d(d+1)/2) * N * 8 bytes must fit:
+ * N <= 1,398,101 nodes for D2Q9 and N <= 838,860 for D3Q19 / D3Q27; larger
+ * grids return LB_E_TOO_LARGE before any GPU work.  The first call on a
+ * device looks up the array's device address (make it before any stream
+ * capture).  Calls that overlap on the GPU race on the shared array: order
+ * them on one stream.  Errors: LB_E_INVAL, LB_E_TOO_LARGE, LB_E_UNSUPPORTED
+ * (internal y or z extent above 65535), LB_E_CUDA. */
+#define LB_NOALLOC_SCRATCH_BYTES (64ull << 20)
+LB_API int lb_step_noalloc(int32_t lattice, const int64_t dims[3], double tau, const lb_boundary* bnd,
+                           double rho0, const double force[3], double* f, int64_t n, void* stream);
 
 /* Human-readable name of a status code. */
 LB_API const char* lb_status_string(int code);

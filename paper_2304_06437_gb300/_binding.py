@@ -19,6 +19,8 @@ LB_E_CUDA = -3
 LB_E_DIVERGED = -4
 LB_E_TIMEOUT = -5
 LB_E_UNSUPPORTED = -6
+LB_E_TOO_LARGE = -7
+LB_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 LB_D2Q9, LB_D3Q19, LB_D3Q27 = 0, 1, 2
 LB_PERIODIC, LB_WALL, LB_MOVING_WALL = 0, 1, 2
@@ -103,6 +105,8 @@ SIGNATURES = {
     "lb_info": (ctypes.c_int, [_vp, _P(lb_info_t)]),
     "lb_lattice_table": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_int32), _dp, _P(ctypes.c_int32)]),
     "lb_memory_plan": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P(lb_memory_plan_t)]),
+    "lb_step_noalloc": (ctypes.c_int, [ctypes.c_int32, _i64p, ctypes.c_double, _P(lb_boundary), ctypes.c_double,
+                                       _dp, _vp, ctypes.c_int64, _vp]),
     "lb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lb_abi_version": (ctypes.c_int, []),
 }

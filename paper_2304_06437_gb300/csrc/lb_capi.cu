@@ -142,6 +142,7 @@ const char* lb_status_string(int code) {
     case LB_E_DIVERGED: return "non-finite state (diverged)";
     case LB_E_TIMEOUT: return "kernel wait timed out";
     case LB_E_UNSUPPORTED: return "unsupported by this build";
+    case LB_E_TOO_LARGE: return "grid exceeds the no-allocation scratch size";
     default: return "unknown status";
   }
 }

@@ -70,6 +70,7 @@ namespace lbgb {
 // ---- two-pass scheme (lb_k0.cu)
 cudaError_t k0_step(lb_ctx* ctx);
 size_t k0_aux_bytes(const Geometry& g, int storage);
+cudaError_t k0_step_buffers(const Geometry& g, double* ft, double* mom, cudaStream_t stream);
 
 // ---- fused scheme (lb_k1_*.cu)
 bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPlan* plan);

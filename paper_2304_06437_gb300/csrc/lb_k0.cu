@@ -139,6 +139,35 @@ size_t k0_aux_bytes(const Geometry& g, int storage) {
   return static_cast<size_t>(m) * static_cast<size_t>(g.vol) * rb;
 }
 
+// The same two kernels on caller-provided FP64 buffers (shifted populations
+// and moment arrays, both laid out with g.pitch / g.vol) on a given stream.
+cudaError_t k0_step_buffers(const Geometry& g, double* ft, double* mom, cudaStream_t stream) {
+  if (g.ny > 65535 || g.nz > 65535) return cudaErrorInvalidConfiguration;
+  cudaError_t err = cudaErrorInvalidValue;
+  dispatch_lattice(g.lattice, [&](auto Lt) {
+    using L = decltype(Lt);
+    auto go = [&](auto force_tag) {
+      constexpr bool FORCE = decltype(force_tag)::value;
+      K0Args<double> args;
+      args.ph = make_phys<double>(g);
+      args.nx = g.nx;
+      args.ny = g.ny;
+      args.nz = g.nz;
+      args.pitch = g.pitch;
+      args.vol = g.vol;
+      for (int k = 0; k < 3; ++k) args.per[k] = g.per[k];
+      make_bounce_terms<L, double>(g, args.bb);
+      dim3 grid(div_up(g.nx, 256), g.ny, g.nz);
+      k0_moments<L, double, double, FORCE><<<grid, 256, 0, stream>>>(args, ft, mom);
+      k0_rebuild<L, double, double, FORCE><<<grid, 256, 0, stream>>>(args, mom, ft);
+      err = cudaGetLastError();
+    };
+    if (g.has_force) go(std::true_type{});
+    else go(std::false_type{});
+  });
+  return err;
+}
+
 cudaError_t k0_step(lb_ctx* ctx) {
   cudaError_t err = cudaErrorInvalidValue;
   if (ctx->g.ny > 65535 || ctx->g.nz > 65535) return cudaErrorInvalidConfiguration;
