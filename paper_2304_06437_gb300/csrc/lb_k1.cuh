@@ -10,24 +10,27 @@
 //
 //   * the grid is cut into brick columns of bx x by nodes and bz planes; a CTA
 //     owns one brick and is the only reader and writer of its populations in
-//     a launch, so in-place update is race free;
+//     a launch, so the in-place update is race free;
 //   * the CTA sweeps its planes along z.  TMA streams plane z + NS of the
-//     population array into a ring of shared-memory slots (mbarrier complete-
-//     tx), every thread collides its node of plane z (lb_collide.cuh) into a
-//     shared window, and then gathers, for each direction a, the collided
-//     value of its upstream neighbour (x - c_a) from the window.  The value
-//     belongs to destination plane z + c_az, so each thread keeps three planes
-//     of partially gathered populations in registers and writes plane z - 1
-//     once it is complete;
-//   * populations whose upstream node lies in another brick come from a small
-//     "shell" buffer: after finishing a boundary node, its owner collides the
-//     new state once more and exports the outgoing populations (those whose
-//     c_a points out of the brick) into the other parity of the shell, which
-//     neighbouring bricks read in the NEXT launch.  Only boundary populations
-//     travel through the shell; there is no second population array and no
-//     full-size moment array;
-//   * halfway bounce-back (and the moving-wall term) is applied where the
-//     upstream point lies outside a non-periodic face.
+//     population array into a ring of shared-memory slots (mbarrier
+//     complete-tx); every thread collides its node of plane z
+//     (lb_collide.cuh) into a padded shared window whose one-node ring holds
+//     the collided populations of the neighbouring bricks (from the shell, see
+//     below); each thread then gathers, for each direction a, the value of
+//     its upstream neighbour x - c_a with no branches.  The value belongs to
+//     destination plane z + c_az, so three destination planes live in
+//     registers and plane z - 1 is stored once complete.  Populations that do
+//     not move laterally (rest, +-z) never leave the registers;
+//   * cross-brick exchange: after finishing a boundary node, its owner
+//     collides the new state once more and exports the populations whose c_a
+//     points out of the brick into the other parity of a small "shell"
+//     buffer, which neighbouring bricks read in the NEXT launch.  The lateral
+//     boundary nodes of a plane are staged in shared memory and exported by a
+//     few whole warps, so no warp diverges on its edge lanes; the bottom and
+//     top planes of a brick export along z with every thread;
+//   * halfway bounce-back (and the moving-wall term) overwrites the gathered
+//     value where the upstream point lies outside a non-periodic face, in a
+//     pass that only threads next to a wall take.
 // Every wait is bounded; on timeout the CTA records LB_E_TIMEOUT in a status
 // word, drains its own outstanding copies (bounded) and exits.
 #pragma once
@@ -59,6 +62,32 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
 __host__ __device__ constexpr size_t align128(size_t v) { return (v + 127) & ~size_t(127); }
 
+// lateral directions (moving along x or y) get a plane of the shared window
+template <class L>
+LB_HD constexpr bool is_lateral(int a) { return L::cx(a) != 0 || L::cy(a) != 0; }
+template <class L>
+LB_HD constexpr int n_lateral() {
+  int n = 0;
+  for (int a = 0; a < L::Q; ++a) n += is_lateral<L>(a) ? 1 : 0;
+  return n;
+}
+template <class L>
+LB_HD constexpr int lat_index(int a) {
+  int n = 0;
+  for (int b = 0; b < a; ++b) n += is_lateral<L>(b) ? 1 : 0;
+  return n;
+}
+// the ia-th direction whose component along axis is sign
+template <class L>
+LB_HD constexpr int dir_of_sub(int axis, int sign, int ia) {
+  for (int a = 0; a < L::Q; ++a)
+    if (comp<L>(axis, a) == sign) {
+      if (ia == 0) return a;
+      --ia;
+    }
+  return -1;
+}
+
 template <class L, class S, class R, int BX, int BY, int NS>
 struct K1Shape {
   static constexpr int Q = L::Q;
@@ -66,16 +95,115 @@ struct K1Shape {
   static constexpr int NXF = count_dirs<L>(0, 1);
   static constexpr int NYF = count_dirs<L>(1, 1);
   static constexpr int NZF = count_dirs<L>(2, 1);
-  static constexpr int HW = NXF * (BY + 2);  // west (and east) halo entries
-  static constexpr int HS = NYF * BX;        // south (and north) halo entries
+  static constexpr int NLAT = n_lateral<L>();
+  static constexpr int PY = NYF > 0 ? 1 : 0;  // window padding rows (none without y motion)
+  static constexpr int WX = BX + 2;
+  static constexpr int WY = BY + 2 * PY;
+  static constexpr int HW = NXF * WY;  // west (and east) ring entries
+  static constexpr int HS = NYF * BX;  // south (and north) ring entries
   static constexpr int H = 2 * HW + 2 * HS;
   static constexpr int HPT = (H + NT - 1) / NT;
+  static constexpr int PMAX = NYF > 0 ? 2 * BX + 2 * (BY - 2) : 2;  // lateral perimeter nodes
+  static constexpr int NEXW = (PMAX + 31) / 32;                     // export warps
   static constexpr size_t SLOT = size_t(Q) * BY * BX * sizeof(S);
+  static constexpr size_t WIN = size_t(NLAT) * WY * WX * sizeof(R);
+  static constexpr size_t STAGE = size_t(Q) * PMAX * sizeof(R);
   static constexpr size_t OFF_WIN = align128(NS * SLOT);
-  static constexpr size_t OFF_HALO = OFF_WIN + align128(size_t(Q) * BY * BX * sizeof(R));
-  static constexpr size_t OFF_BAR = OFF_HALO + align128(size_t(H > 0 ? H : 1) * sizeof(R));
+  static constexpr size_t OFF_STAGE = OFF_WIN + align128(WIN);
+  static constexpr size_t OFF_BAR = OFF_STAGE + align128(2 * STAGE);
   static constexpr size_t SMEM = OFF_BAR + align128(NS * sizeof(uint64_t));
+  static_assert(BY == 1 || NYF > 0, "a 2D brick has one internal row");
+  static_assert(PMAX <= NT, "perimeter larger than the CTA");
 };
+
+// index of the lateral perimeter node (tx, ty) of an active bxa x bya brick
+template <int NYF>
+__device__ __forceinline__ int perimeter_index(int tx, int ty, int bxa, int bya) {
+  if (NYF == 0) return (tx == 0) ? 0 : (tx == bxa - 1 ? 1 : -1);
+  const int m = bxa >= 2 ? 2 : 1;
+  if (ty == 0) return tx;
+  if (ty == bya - 1) return bxa + tx;
+  if (tx == 0) return bxa * 2 + (ty - 1) * m;
+  if (tx == bxa - 1) return bxa * 2 + (ty - 1) * m + 1;
+  return -1;
+}
+template <int NYF>
+__device__ __forceinline__ int perimeter_count(int bxa, int bya) {
+  if (NYF == 0) return bxa >= 2 ? 2 : 1;
+  const int m = bxa >= 2 ? 2 : 1;
+  return bxa * (bya >= 2 ? 2 : 1) + (bya > 2 ? bya - 2 : 0) * m;
+}
+template <int NYF>
+__device__ __forceinline__ void perimeter_node(int p, int bxa, int bya, int& tx, int& ty) {
+  if (NYF == 0) {
+    tx = (p == 0) ? 0 : bxa - 1;
+    ty = 0;
+    return;
+  }
+  const int m = bxa >= 2 ? 2 : 1;
+  if (p < bxa) {
+    tx = p;
+    ty = 0;
+  } else if (bya >= 2 && p < 2 * bxa) {
+    tx = p - bxa;
+    ty = bya - 1;
+  } else {
+    const int q = p - bxa * (bya >= 2 ? 2 : 1);
+    ty = 1 + q / m;
+    tx = (q % m == 0) ? 0 : bxa - 1;
+  }
+}
+
+// Collide the completed (rounded) state of one node once more and export the
+// populations that leave the brick through the flagged faces.
+template <class L, class S, class R, bool FORCE>
+__device__ __forceinline__ void export_node(const K1Args<R>& args, const R (&fin)[L::Q], int x, int y, int zd,
+                                            bool eW, bool eE, bool eS, bool eN, bool eD, bool eU, int bI, int bJ,
+                                            int bK) {
+  constexpr int NXF = count_dirs<L>(0, 1), NYF = count_dirs<L>(1, 1), NZF = count_dirs<L>(2, 1);
+  R fr[L::Q];
+  static_for<0, L::Q>([&](auto A_) {
+    constexpr int a = decltype(A_)::value;
+    fr[a] = round_to_storage<S, R>(fin[a]);
+  });
+  Mom<R> m;
+  moments<L, R, FORCE>(fr, args.ph, m);
+  Coef<R> kc;
+  coeffs<L, R, FORCE>(m, args.ph, kc);
+  R* shn = args.sh_next;
+  const int nx = args.nx, ny = args.ny, nz = args.nz;
+  static_for<0, L::Q>([&](auto A_) {
+    constexpr int a = decltype(A_)::value;
+    constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+    const bool wx = (cx == -1 && eW) || (cx == 1 && eE);
+    const bool wy = (cy == -1 && eS) || (cy == 1 && eN);
+    const bool wz = (cz == -1 && eD) || (cz == 1 && eU);
+    if (wx || wy || wz) {
+      const R v = post<L, R, a>(kc);
+      if constexpr (cx != 0) {
+        if (wx) {
+          constexpr int side = cx == 1 ? 1 : 0;
+          constexpr int ia = sub_index<L>(0, cx, a);
+          shn[args.sx_off + ((int64_t(side) * args.nbx + bI) * NXF + ia) * int64_t(nz) * ny + int64_t(zd) * ny + y] = v;
+        }
+      }
+      if constexpr (cy != 0) {
+        if (wy) {
+          constexpr int side = cy == 1 ? 1 : 0;
+          constexpr int ia = sub_index<L>(1, cy, a);
+          shn[args.sy_off + ((int64_t(side) * args.nby + bJ) * NYF + ia) * int64_t(nz) * nx + int64_t(zd) * nx + x] = v;
+        }
+      }
+      if constexpr (cz != 0) {
+        if (wz) {
+          constexpr int side = cz == 1 ? 1 : 0;
+          constexpr int ia = sub_index<L>(2, cz, a);
+          shn[args.sz_off + ((int64_t(side) * args.nbz + bK) * NZF + ia) * int64_t(ny) * nx + int64_t(y) * nx + x] = v;
+        }
+      }
+    }
+  });
+}
 
 template <class L, class S, class R, int BX, int BY, int NS, bool FORCE>
 __global__ void __launch_bounds__(BX* BY, 1)
@@ -84,17 +212,21 @@ __global__ void __launch_bounds__(BX* BY, 1)
   constexpr int Q = L::Q;
   constexpr int NT = Sh::NT;
   constexpr int NXF = Sh::NXF, NYF = Sh::NYF, NZF = Sh::NZF;
+  constexpr int PY = Sh::PY, WX = Sh::WX, WY = Sh::WY;
   constexpr int HW = Sh::HW, HS = Sh::HS, H = Sh::H, HPT = Sh::HPT;
+  constexpr int PMAX = Sh::PMAX, NEXW = Sh::NEXW;
+  constexpr int WPLANE = WY * WX;
 
   extern __shared__ __align__(128) unsigned char smem[];
   S* slots = reinterpret_cast<S*>(smem);
   R* win = reinterpret_cast<R*>(smem + Sh::OFF_WIN);
-  R* halo = reinterpret_cast<R*>(smem + Sh::OFF_HALO);
+  R* stage = reinterpret_cast<R*>(smem + Sh::OFF_STAGE);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Sh::OFF_BAR);
 
   const int tid = threadIdx.x;
   const int tx = tid % BX;
   const int ty = tid / BX;
+  const int warp = tid / 32, lane = tid % 32;
   const int nx = args.nx, ny = args.ny, nz = args.nz;
   const int nbx = args.nbx, nby = args.nby, nbz = args.nbz;
   const int bI = blockIdx.x % nbx;
@@ -117,16 +249,17 @@ __global__ void __launch_bounds__(BX* BY, 1)
   const int bJs = (bJ + nby - 1) % nby, bJn = (bJ + 1) % nby;
   const int bKd = (bK + nbz - 1) % nbz, bKu = (bK + 1) % nbz;
 
-  // bounce-back predicates of this node (x, y axes): the upstream point of a
-  // direction with c = +1 is x - 1, which leaves a non-periodic low face at x = 0
-  const bool bxlo = (x == 0) && !args.per[0];
-  const bool bxhi = (x == nx - 1) && !args.per[0];
-  const bool bylo = (y == 0) && !args.per[1];
-  const bool byhi = (y == ny - 1) && !args.per[1];
+  // bounce-back predicates of this node along x and y: the upstream point of
+  // a direction with c = +1 is x - 1, which leaves a non-periodic low face at x = 0
+  const bool bxlo = active && (x == 0) && !args.per[0];
+  const bool bxhi = active && (x == nx - 1) && !args.per[0];
+  const bool bylo = active && (y == 0) && !args.per[1];
+  const bool byhi = active && (y == ny - 1) && !args.per[1];
+  const bool xy_wall = bxlo || bxhi || bylo || byhi;
+  const bool z_walls = !args.per[2];
 
   S* __restrict__ fglob = static_cast<S*>(args.f);
   const R* __restrict__ shc = args.sh_cur;
-  R* __restrict__ shn = args.sh_next;
 
   // ---------------------------------------------------------------- setup
   if (tid == 0) {
@@ -147,9 +280,10 @@ __global__ void __launch_bounds__(BX* BY, 1)
     }
   }
 
-  // halo descriptors: entry h -> (global base offset, z stride, smem index)
+  // ring entries of the window: entry h -> (global base, z stride, window index)
   int64_t hbase[HPT];
-  int64_t hzs[HPT];
+  int hzs[HPT];
+  int hsm[HPT];
   bool hval[HPT];
 #pragma unroll
   for (int e = 0; e < HPT; ++e) {
@@ -157,24 +291,28 @@ __global__ void __launch_bounds__(BX* BY, 1)
     hval[e] = false;
     hbase[e] = 0;
     hzs[e] = 1;
+    hsm[e] = 0;
     if (h < H) {
       if (h < 2 * HW) {
         const bool west = h < HW;
         const int hh = west ? h : h - HW;
-        const int ia = hh / (BY + 2);
-        const int j = hh % (BY + 2);
-        int sy = y0 - 1 + j;
-        bool ok = west ? nbW : nbE;
+        const int ia = hh / WY;
+        const int r = hh % WY;  // window row; source y = y0 - PY + r
+        int sy = y0 - PY + r;
+        bool ok = (west ? nbW : nbE) && r < bya + 2 * PY;
         if (sy < 0 || sy >= ny) {
           if (args.per[1]) sy = (sy + ny) % ny;
           else ok = false;
         }
-        // west halo reads the high-face export (side 1) of the west brick
+        const int a = dir_of_sub<L>(0, west ? 1 : -1, ia);
+        const int col = west ? 0 : bxa + 1;
+        // the west ring holds the high-face export (side 1) of the west brick
         const int side = west ? 1 : 0;
         const int bb = west ? bIw : bIe;
         hval[e] = ok;
         hbase[e] = args.sx_off + ((int64_t(side) * nbx + bb) * NXF + ia) * int64_t(nz) * ny + sy;
         hzs[e] = ny;
+        hsm[e] = lat_index<L>(a) * WPLANE + r * WX + col;
       } else {
         const int h2 = h - 2 * HW;
         const bool south = h2 < HS;
@@ -182,16 +320,17 @@ __global__ void __launch_bounds__(BX* BY, 1)
         const int ia = hh / BX;
         const int i = hh % BX;
         const bool ok = (south ? nbS : nbN) && i < bxa;
+        const int a = dir_of_sub<L>(1, south ? 1 : -1, ia);
+        const int row = south ? 0 : bya + 1;
         const int side = south ? 1 : 0;
         const int bb = south ? bJs : bJn;
         hval[e] = ok;
         hbase[e] = args.sy_off + ((int64_t(side) * nby + bb) * NYF + ia) * int64_t(nz) * nx + x0 + i;
         hzs[e] = nx;
+        hsm[e] = lat_index<L>(a) * WPLANE + row * WX + 1 + i;
       }
     }
   }
-  (void)HS;
-  (void)NZF;
 
   auto plane_needed = [&](int z) -> bool {
     if (z >= z0 && z < z1) return true;
@@ -199,17 +338,24 @@ __global__ void __launch_bounds__(BX* BY, 1)
     if (z == z1) return nbU;
     return false;
   };
-  auto wrap_z = [&](int z) -> int { return (z + nz) % nz; };
 
   R hreg[HPT];
   auto halo_fetch = [&](int z) {
-    const int zw = wrap_z(z);
+    const int zw = (z + nz) % nz;
 #pragma unroll
     for (int e = 0; e < HPT; ++e) hreg[e] = hval[e] ? shc[hbase[e] + int64_t(zw) * hzs[e]] : R(0);
   };
   if (plane_needed(z0 - 1)) halo_fetch(z0 - 1);
 
-  // three destination planes of partially gathered populations
+  // perimeter (lateral boundary) slot of this node, and export-warp work
+  const int pidx = active ? perimeter_index<NYF>(tx, ty, bxa, bya) : -1;
+  const int pcount = perimeter_count<NYF>(bxa, bya);
+  const bool any_lateral_export = nbW || nbE || (NYF > 0 && (nbS || nbN));
+
+  // this thread's own cell in the window (interior of the padding ring)
+  const int wbase = (ty + PY) * WX + (tx + 1);
+
+  // three destination planes of gathered populations
   R G0[Q], G1[Q], G2[Q];  // planes z-1, z, z+1
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
@@ -217,6 +363,13 @@ __global__ void __launch_bounds__(BX* BY, 1)
     G1[a] = R(0);
     G2[a] = R(0);
   }
+  // bounce-back values of the z-descending directions of the previous plane;
+  // applied after the next gather, which would otherwise overwrite them
+  constexpr int NDN = count_dirs<L>(2, -1);
+  R bdn[NDN];
+  unsigned bdn_mask = 0;
+#pragma unroll
+  for (int i = 0; i < NDN; ++i) bdn[i] = R(0);
 
   const int n_it = (z1 - z0) + 2;
   for (int it = 0; it < n_it; ++it) {
@@ -226,21 +379,22 @@ __global__ void __launch_bounds__(BX* BY, 1)
     const int k = z - z0;
     const int slot = real ? (k % NS) : 0;
     bool timeout = false;
+    R own[Q];  // this node's collided populations (real planes)
 
     // ---------------------------------------------- phase 1: window of plane z
     if (real) {
       if (!mbar_wait_bounded(&bars[slot], (k / NS) & 1, kWaitLimitNs)) timeout = true;
       if (!timeout && active) {
         const S* sl = slots + size_t(slot) * Q * BY * BX + ty * BX + tx;
-        R fl[Q], fs[Q];
+        R fl[Q];
         static_for<0, Q>([&](auto A_) {
           constexpr int a = decltype(A_)::value;
           fl[a] = load_as<S, R>(sl[a * BY * BX]);
         });
-        collide<L, R, FORCE>(fl, args.ph, fs);
+        collide<L, R, FORCE>(fl, args.ph, own);
         static_for<0, Q>([&](auto A_) {
           constexpr int a = decltype(A_)::value;
-          win[(a * BY + ty) * BX + tx] = fs[a];
+          if constexpr (is_lateral<L>(a)) win[lat_index<L>(a) * WPLANE + wbase] = own[a];
         });
       }
     } else if (need && active) {
@@ -248,22 +402,27 @@ __global__ void __launch_bounds__(BX* BY, 1)
       const bool low = (z == z0 - 1);
       const int side = low ? 1 : 0;
       const int bb = low ? bKd : bKu;
+      const int64_t base = args.sz_off + (int64_t(side) * nbz + bb) * NZF * int64_t(ny) * nx + int64_t(y) * nx + x;
       static_for<0, Q>([&](auto A_) {
         constexpr int a = decltype(A_)::value;
         constexpr int cz = L::cz(a);
+        own[a] = R(0);
         if constexpr (cz != 0) {
           if ((cz == 1) == low) {
             constexpr int iz = sub_index<L>(2, cz, a);
-            win[(a * BY + ty) * BX + tx] =
-                shc[args.sz_off + ((int64_t(side) * nbz + bb) * NZF + iz) * int64_t(ny) * nx + int64_t(y) * nx + x];
+            const R v = shc[base + int64_t(iz) * ny * nx];
+            if constexpr (is_lateral<L>(a)) win[lat_index<L>(a) * WPLANE + wbase] = v;
+            else own[a] = v;
           }
         }
       });
     }
     if (need) {
+      // only valid entries: an invalid north/south entry of a ragged brick
+      // would alias the east ring's corner cell of a diagonal direction
 #pragma unroll
       for (int e = 0; e < HPT; ++e)
-        if (tid + e * NT < H) halo[tid + e * NT] = hreg[e];
+        if (hval[e]) win[hsm[e]] = hreg[e];
     }
     if (z + 1 <= z1 && plane_needed(z + 1)) halo_fetch(z + 1);
 
@@ -287,126 +446,95 @@ __global__ void __launch_bounds__(BX* BY, 1)
       }
     }
 
-    // ---------------------------------------------- phase 2: gather
+    // ---------------------------------------------- phase 2: gather (no branches)
     if (active && need) {
-      const bool bzlo_z = (z == 0) && !args.per[2];
-      const bool bzhi_z = (z == nz - 1) && !args.per[2];
       static_for<0, Q>([&](auto A_) {
         constexpr int a = decltype(A_)::value;
         constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
-        // x / y part of the bounce-back combo of direction a at this node
-        int cxy = 0;
-        if constexpr (cx == 1) cxy |= bxlo ? 1 : 0;
-        if constexpr (cx == -1) cxy |= bxhi ? 1 : 0;
-        if constexpr (cy == 1) cxy |= bylo ? 2 : 0;
-        if constexpr (cy == -1) cxy |= byhi ? 2 : 0;
-        // pull for destination plane zd = z + cz from the window of plane z
-        const int zd = z + cz;
-        if (zd >= z0 && zd < z1) {
-          int cb = cxy;
-          if constexpr (cz == 1) cb |= ((zd == 0) && !args.per[2]) ? 4 : 0;
-          if constexpr (cz == -1) cb |= ((zd == nz - 1) && !args.per[2]) ? 4 : 0;
-          if (cb == 0) {
-            R v;
-            bool done = false;
-            if constexpr (cx == 1) {
-              if (tx == 0) {
-                v = halo[sub_index<L>(0, 1, a) * (BY + 2) + (ty - cy + 1)];
-                done = true;
-              }
-            }
-            if constexpr (cx == -1) {
-              if (tx == bxa - 1) {
-                v = halo[HW + sub_index<L>(0, -1, a) * (BY + 2) + (ty - cy + 1)];
-                done = true;
-              }
-            }
-            if constexpr (cy == 1) {
-              if (!done && ty == 0) {
-                v = halo[2 * HW + sub_index<L>(1, 1, a) * BX + (tx - cx)];
-                done = true;
-              }
-            }
-            if constexpr (cy == -1) {
-              if (!done && ty == bya - 1) {
-                v = halo[2 * HW + HS + sub_index<L>(1, -1, a) * BX + (tx - cx)];
-                done = true;
-              }
-            }
-            if (!done) v = win[(a * BY + (ty - cy)) * BX + (tx - cx)];
-            if constexpr (cz == -1) G0[a] = v;
-            if constexpr (cz == 0) G1[a] = v;
-            if constexpr (cz == 1) G2[a] = v;
-          }
-        }
-        // halfway bounce-back into plane z (own node, real planes only)
-        if (real) {
-          int cb = cxy;
-          if constexpr (cz == 1) cb |= bzlo_z ? 4 : 0;
-          if constexpr (cz == -1) cb |= bzhi_z ? 4 : 0;
-          constexpr int oa = L::opp(a);
-          if (cb != 0) G1[a] = win[(oa * BY + ty) * BX + tx] + args.bb[a][cb];
+        R v;
+        if constexpr (is_lateral<L>(a)) v = win[lat_index<L>(a) * WPLANE + wbase - cy * WX - cx];
+        else v = own[a];
+        if constexpr (cz == -1) G0[a] = v;
+        if constexpr (cz == 0) G1[a] = v;
+        if constexpr (cz == 1) G2[a] = v;
+      });
+    }
+    // z-descending bounce-backs of plane z - 1, saved one plane ago
+    if (bdn_mask) {
+      static_for<0, Q>([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        if constexpr (L::cz(a) == -1) {
+          constexpr int i = sub_index<L>(2, -1, a);
+          if (bdn_mask >> i & 1) G0[a] = bdn[i];
         }
       });
+      bdn_mask = 0;
+    }
+    // halfway bounce-back for destination plane z (threads next to a wall)
+    if (real && active && (xy_wall || (z_walls && (z == 0 || z == nz - 1)))) {
+      const bool bzlo = z_walls && z == 0, bzhi = z_walls && z == nz - 1;
+      static_for<0, Q>([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+        int cb = 0;
+        if constexpr (cx == 1) cb |= bxlo ? 1 : 0;
+        if constexpr (cx == -1) cb |= bxhi ? 1 : 0;
+        if constexpr (cy == 1) cb |= bylo ? 2 : 0;
+        if constexpr (cy == -1) cb |= byhi ? 2 : 0;
+        if constexpr (cz == 1) cb |= bzlo ? 4 : 0;
+        if constexpr (cz == -1) cb |= bzhi ? 4 : 0;
+        if (cb != 0) {
+          constexpr int oa = L::opp(a);
+          R back;
+          if constexpr (is_lateral<L>(oa)) back = win[lat_index<L>(oa) * WPLANE + wbase];
+          else back = own[oa];
+          const R v = back + args.bb[a][cb];
+          if constexpr (cz == -1) {
+            constexpr int i = sub_index<L>(2, -1, a);
+            bdn[i] = v;
+            bdn_mask |= 1u << i;
+          } else {
+            G1[a] = v;
+          }
+        }
+      });
+    }
+
+    // ---------------------------------------------- exports of plane z - 2
+    const int zx = z - 2;  // staged one iteration ago
+    if (any_lateral_export && warp < NEXW && zx >= z0 && zx < z1) {
+      const int p = warp * 32 + lane;
+      if (p < pcount) {
+        int ptx, pty;
+        perimeter_node<NYF>(p, bxa, bya, ptx, pty);
+        const R* st = stage + (zx & 1) * (Q * PMAX) + p;
+        R fin[Q];
+        static_for<0, Q>([&](auto A_) {
+          constexpr int a = decltype(A_)::value;
+          fin[a] = st[a * PMAX];
+        });
+        export_node<L, S, R, FORCE>(args, fin, x0 + ptx, y0 + pty, zx, ptx == 0 && nbW, ptx == bxa - 1 && nbE,
+                                    pty == 0 && nbS, pty == bya - 1 && nbN, false, false, bI, bJ, bK);
+      }
     }
 
     // ---------------------------------------------- plane z - 1 is complete
     const int zd = z - 1;
     if (active && zd >= z0 && zd < z1) {
       const int64_t o = x + args.pitch * (y + int64_t(ny) * zd);
-      S st[Q];
       static_for<0, Q>([&](auto A_) {
         constexpr int a = decltype(A_)::value;
-        st[a] = store_as<S, R>(G0[a]);
-        fglob[a * args.vol + o] = st[a];
+        fglob[a * args.vol + o] = store_as<S, R>(G0[a]);
       });
-      const bool eW = tx == 0 && nbW, eE = tx == bxa - 1 && nbE;
-      const bool eS = ty == 0 && nbS, eN = ty == bya - 1 && nbN;
-      const bool eD = zd == z0 && nbD, eU = zd == z1 - 1 && nbU;
-      if (eW || eE || eS || eN || eD || eU) {
-        // collide the stored (rounded) state once more and export the
-        // populations that leave the brick; the next launch reads them
-        R fr[Q];
+      if (pidx >= 0 && any_lateral_export) {
+        R* st = stage + (zd & 1) * (Q * PMAX) + pidx;
         static_for<0, Q>([&](auto A_) {
           constexpr int a = decltype(A_)::value;
-          fr[a] = load_as<S, R>(st[a]);
-        });
-        Mom<R> m;
-        moments<L, R, FORCE>(fr, args.ph, m);
-        Coef<R> kc;
-        coeffs<L, R, FORCE>(m, args.ph, kc);
-        static_for<0, Q>([&](auto A_) {
-          constexpr int a = decltype(A_)::value;
-          constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
-          const bool wx = (cx == -1 && eW) || (cx == 1 && eE);
-          const bool wy = (cy == -1 && eS) || (cy == 1 && eN);
-          const bool wz = (cz == -1 && eD) || (cz == 1 && eU);
-          if (wx || wy || wz) {
-            const R v = post<L, R, a>(kc);
-            if constexpr (cx != 0) {
-              if (wx) {
-                constexpr int side = cx == 1 ? 1 : 0;
-                constexpr int ia = sub_index<L>(0, cx, a);
-                shn[args.sx_off + ((int64_t(side) * nbx + bI) * NXF + ia) * int64_t(nz) * ny + int64_t(zd) * ny + y] = v;
-              }
-            }
-            if constexpr (cy != 0) {
-              if (wy) {
-                constexpr int side = cy == 1 ? 1 : 0;
-                constexpr int ia = sub_index<L>(1, cy, a);
-                shn[args.sy_off + ((int64_t(side) * nby + bJ) * NYF + ia) * int64_t(nz) * nx + int64_t(zd) * nx + x] = v;
-              }
-            }
-            if constexpr (cz != 0) {
-              if (wz) {
-                constexpr int side = cz == 1 ? 1 : 0;
-                constexpr int ia = sub_index<L>(2, cz, a);
-                shn[args.sz_off + ((int64_t(side) * nbz + bK) * NZF + ia) * int64_t(ny) * nx + int64_t(y) * nx + x] = v;
-              }
-            }
-          }
+          st[a * PMAX] = G0[a];
         });
       }
+      const bool eD = zd == z0 && nbD, eU = zd == z1 - 1 && nbU;
+      if (eD || eU) export_node<L, S, R, FORCE>(args, G0, x, y, zd, false, false, false, false, eD, eU, bI, bJ, bK);
     }
     // rotate the destination planes
 #pragma unroll
@@ -416,6 +544,24 @@ __global__ void __launch_bounds__(BX* BY, 1)
     }
     __syncthreads();
   }
+
+  // exports of the last plane (staged in the final iteration)
+  const int zx = z1 - 1;
+  if (any_lateral_export && warp < NEXW && zx >= z0) {
+    const int p = warp * 32 + lane;
+    if (p < pcount) {
+      int ptx, pty;
+      perimeter_node<NYF>(p, bxa, bya, ptx, pty);
+      const R* st = stage + (zx & 1) * (Q * PMAX) + p;
+      R fin[Q];
+      static_for<0, Q>([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        fin[a] = st[a * PMAX];
+      });
+      export_node<L, S, R, FORCE>(args, fin, x0 + ptx, y0 + pty, zx, ptx == 0 && nbW, ptx == bxa - 1 && nbE,
+                                  pty == 0 && nbS, pty == bya - 1 && nbN, false, false, bI, bJ, bK);
+    }
+  }
 }
 
 // Shell bootstrap: collide every brick-boundary node of the current state and
@@ -424,7 +570,6 @@ __global__ void __launch_bounds__(BX* BY, 1)
 template <class L, class S, class R, int BX, int BY, bool FORCE>
 __global__ void __launch_bounds__(256) k1_bootstrap(const __grid_constant__ K1Args<R> args) {
   constexpr int Q = L::Q;
-  constexpr int NXF = count_dirs<L>(0, 1), NYF = count_dirs<L>(1, 1), NZF = count_dirs<L>(2, 1);
   const int64_t n = int64_t(args.nx) * args.ny * args.nz;
   for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < n; idx += int64_t(gridDim.x) * blockDim.x) {
     const int x = int(idx % args.nx);
@@ -447,43 +592,7 @@ __global__ void __launch_bounds__(256) k1_bootstrap(const __grid_constant__ K1Ar
       constexpr int a = decltype(A_)::value;
       fr[a] = load_as<S, R>(fg[a * args.vol + o]);
     });
-    Mom<R> m;
-    moments<L, R, FORCE>(fr, args.ph, m);
-    Coef<R> kc;
-    coeffs<L, R, FORCE>(m, args.ph, kc);
-    R* shn = args.sh_next;
-    const int nx = args.nx, ny = args.ny, nz = args.nz;
-    static_for<0, Q>([&](auto A_) {
-      constexpr int a = decltype(A_)::value;
-      constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
-      const bool wx = (cx == -1 && eW) || (cx == 1 && eE);
-      const bool wy = (cy == -1 && eS) || (cy == 1 && eN);
-      const bool wz = (cz == -1 && eD) || (cz == 1 && eU);
-      if (wx || wy || wz) {
-        const R v = post<L, R, a>(kc);
-        if constexpr (cx != 0) {
-          if (wx) {
-            constexpr int side = cx == 1 ? 1 : 0;
-            constexpr int ia = sub_index<L>(0, cx, a);
-            shn[args.sx_off + ((int64_t(side) * args.nbx + bI) * NXF + ia) * int64_t(nz) * ny + int64_t(z) * ny + y] = v;
-          }
-        }
-        if constexpr (cy != 0) {
-          if (wy) {
-            constexpr int side = cy == 1 ? 1 : 0;
-            constexpr int ia = sub_index<L>(1, cy, a);
-            shn[args.sy_off + ((int64_t(side) * args.nby + bJ) * NYF + ia) * int64_t(nz) * nx + int64_t(z) * nx + x] = v;
-          }
-        }
-        if constexpr (cz != 0) {
-          if (wz) {
-            constexpr int side = cz == 1 ? 1 : 0;
-            constexpr int ia = sub_index<L>(2, cz, a);
-            shn[args.sz_off + ((int64_t(side) * args.nbz + bK) * NZF + ia) * int64_t(ny) * nx + int64_t(y) * nx + x] = v;
-          }
-        }
-      }
-    });
+    export_node<L, S, R, FORCE>(args, fr, x, y, z, eW, eE, eS, eN, eD, eU, bI, bJ, bK);
   }
 }
 

@@ -6,7 +6,7 @@
 namespace lbgb {
 
 extern const K1Variant k1_variants_d3q19[] = {
-    K1Impl<D3Q19, float, float, 32,16,3>::variant(LB_D3Q19, LB_F32),
+    K1Impl<D3Q19, float, float, 32,16,4>::variant(LB_D3Q19, LB_F32),
     K1Impl<D3Q19, double, double, 32,8,2>::variant(LB_D3Q19, LB_F64),
     K1Impl<D3Q19, __half, float, 32,16,4>::variant(LB_D3Q19, LB_F16S),
     K1Impl<D3Q19, __nv_bfloat16, float, 32,16,4>::variant(LB_D3Q19, LB_BF16S),
