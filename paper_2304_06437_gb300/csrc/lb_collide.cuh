@@ -14,14 +14,16 @@
 //     A = drho - 3/2 rho0 u.u - 3/2 (1-omega) tr Pi^neq - 3 (1 - omega/2) u.F
 //     B = 3 rho0 u + 3/2 F
 //     C = 9/2 [ rho0 u u + (1-omega) Pi^neq + (1 - omega/2)(u F + F u) ]
+//   (kept as the diagonal C_aa and the doubled off-diagonal 2 C_ab)
 //   This is t_a [drho + rho0 (c.u/cs2 + (cc - cs2 I):uu/(2 cs2^2))]
 //   + (1-omega) t_a [c.j^neq/cs2 + (cc - cs2 I):Pi^neq/(2 cs2^2)] + S_a with
 //   j^neq = -F/2, written as a quadratic form in c_a.
 //
-// Every operation is written out explicitly and the library is compiled with
-// -fmad=false, so the rounding sequence is fixed by this source: the fused
-// kernel, the two-pass kernel and the shell exporter evaluate the same
-// instructions on the same inputs and agree bit for bit.
+// Every operation is written out explicitly (fused multiply-adds through
+// fma_r) and the library is compiled with -fmad=false, so the rounding
+// sequence is fixed by this source: the fused kernel, the two-pass kernel and
+// the shell exporter evaluate the same instructions on the same inputs and
+// agree bit for bit.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -73,7 +75,12 @@ struct Phys {
   R F[3];    // body force (internal axes)
   R hF[3];   // F / 2
   R cs2;     // 1/3 rounded to R
+  // products of the constants above, formed once in FP64 on the host
+  R c15rho0, c15om1, c3rho0, c45rho0, c45om1, c9rho0, c9om1, c3g, c9g;
 };
+
+LB_DEV float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
+LB_DEV double fma_r(double a, double b, double c) { return fma(a, b, c); }
 
 template <class R>
 struct Mom {
@@ -155,17 +162,16 @@ LB_DEV void moments(const R (&f)[L::Q], const Phys<R>& ph, Mom<R>& m) {
     }
     ru[al] = ph.rho0 * m.u[al];
   });
-  const R dcs = drho * ph.cs2;
   static_for<0, 3>([&](auto AL) {
     constexpr int al = decltype(AL)::value;
-    if constexpr (L::axis(al)) m.pi[al] = (Pd[al] - dcs) - ru[al] * m.u[al];
+    if constexpr (L::axis(al)) m.pi[al] = fma_r(-ru[al], m.u[al], fma_r(-ph.cs2, drho, Pd[al]));
     else m.pi[al] = R(0);
   });
   static_for<0, 3>([&](auto AL) {
     constexpr int al = decltype(AL)::value;
     static_for<al + 1, 3>([&](auto BE) {
       constexpr int be = decltype(BE)::value;
-      if constexpr (L::axis(al) && L::axis(be)) m.pi[3 + od(al, be)] = Po[od(al, be)] - ru[al] * m.u[be];
+      if constexpr (L::axis(al) && L::axis(be)) m.pi[3 + od(al, be)] = fma_r(-ru[al], m.u[be], Po[od(al, be)]);
       else m.pi[3 + od(al, be)] = R(0);
     });
   });
@@ -178,40 +184,39 @@ LB_DEV void coeffs(const Mom<R>& m, const Phys<R>& ph, Coef<R>& k) {
   static_for<0, 3>([&](auto AL) {
     constexpr int al = decltype(AL)::value;
     if constexpr (L::axis(al)) {
-      usq = usq + m.u[al] * m.u[al];
+      usq = fma_r(m.u[al], m.u[al], usq);
       tr = tr + m.pi[al];
-      if constexpr (FORCE) uF = uF + m.u[al] * ph.F[al];
+      if constexpr (FORCE) uF = fma_r(m.u[al], ph.F[al], uF);
     }
   });
-  R A = (m.drho - R(1.5) * (ph.rho0 * usq)) - R(1.5) * (ph.om1 * tr);
-  if constexpr (FORCE) A = A - R(3) * (ph.g * uF);
+  R A = fma_r(-ph.c15om1, tr, fma_r(-ph.c15rho0, usq, m.drho));
+  if constexpr (FORCE) A = fma_r(-ph.c3g, uF, A);
   k.A = A;
   static_for<0, 3>([&](auto AL) {
     constexpr int al = decltype(AL)::value;
-    const R ru = ph.rho0 * m.u[al];
-    R b = R(3) * ru;
-    R c = ru * m.u[al] + ph.om1 * m.pi[al];
+    R b = ph.c3rho0 * m.u[al];
+    R c = fma_r(ph.c45om1, m.pi[al], (ph.c45rho0 * m.u[al]) * m.u[al]);
     if constexpr (FORCE) {
-      b = b + R(1.5) * ph.F[al];
-      c = c + ph.g * (R(2) * (m.u[al] * ph.F[al]));
+      b = fma_r(R(1.5), ph.F[al], b);
+      c = fma_r(ph.c9g, m.u[al] * ph.F[al], c);
     }
     k.B[al] = b;
-    k.C[al] = R(4.5) * c;
+    k.C[al] = c;
   });
   static_for<0, 3>([&](auto AL) {
     constexpr int al = decltype(AL)::value;
     static_for<al + 1, 3>([&](auto BE) {
       constexpr int be = decltype(BE)::value;
-      R c = (ph.rho0 * m.u[al]) * m.u[be] + ph.om1 * m.pi[3 + od(al, be)];
-      if constexpr (FORCE) c = c + ph.g * (m.u[al] * ph.F[be] + ph.F[al] * m.u[be]);
-      k.C2[od(al, be)] = R(9) * c;
+      R c = fma_r(ph.c9om1, m.pi[3 + od(al, be)], (ph.c9rho0 * m.u[al]) * m.u[be]);
+      if constexpr (FORCE) c = fma_r(ph.c9g, fma_r(m.u[al], ph.F[be], ph.F[al] * m.u[be]), c);
+      k.C2[od(al, be)] = c;
     });
   });
 }
 
 // ------------------------------------------------------------ one population
 // ft*_a = t_a (even + odd), even = A + sum_{c_al != 0} C_alal + sum c_al c_be C2,
-// odd = sum c_al B_al
+// odd = sum c_al B_al; evaluated as fma(t_a, even, t_a odd)
 template <class L, class R, int a>
 LB_DEV R post(const Coef<R>& k) {
   R even = k.A;
@@ -242,7 +247,8 @@ LB_DEV R post(const Coef<R>& k) {
     }
   });
   constexpr R w = R(weight<L>(a));
-  return w * (even + odd);
+  if (first) return w * even;  // rest population: no odd part
+  return fma_r(w, even, w * odd);
 }
 
 // full regularized collision of one node: ft -> ft*

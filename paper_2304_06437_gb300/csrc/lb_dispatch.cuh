@@ -49,6 +49,16 @@ Phys<R> make_phys(const Geometry& g) {
     p.hF[k] = R(0.5 * g.force[k]);
   }
   p.cs2 = R(1.0 / 3.0);
+  const double om1 = 1.0 - omega, gg = 1.0 - 0.5 * omega, r0 = g.rho0;
+  p.c15rho0 = R(1.5 * r0);
+  p.c15om1 = R(1.5 * om1);
+  p.c3rho0 = R(3.0 * r0);
+  p.c45rho0 = R(4.5 * r0);
+  p.c45om1 = R(4.5 * om1);
+  p.c9rho0 = R(9.0 * r0);
+  p.c9om1 = R(9.0 * om1);
+  p.c3g = R(3.0 * gg);
+  p.c9g = R(9.0 * gg);
   return p;
 }
 

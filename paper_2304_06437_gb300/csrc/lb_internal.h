@@ -34,6 +34,7 @@ struct FusedPlan {
   int64_t sx_elems, sy_elems, sz_elems;  // per parity
   int64_t parity_elems;
   int slots;               // TMA pipeline depth
+  int wbuf;                // shared window buffers (2: one barrier per plane)
   size_t smem_bytes;
 };
 

@@ -38,6 +38,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "lb_dispatch.cuh"
 #include "lb_ptx.cuh"
 
@@ -88,7 +90,7 @@ LB_HD constexpr int dir_of_sub(int axis, int sign, int ia) {
   return -1;
 }
 
-template <class L, class S, class R, int BX, int BY, int NS>
+template <class L, class S, class R, int BX, int BY, int NS, int WB>
 struct K1Shape {
   static constexpr int Q = L::Q;
   static constexpr int NT = BX * BY;
@@ -99,21 +101,27 @@ struct K1Shape {
   static constexpr int PY = NYF > 0 ? 1 : 0;  // window padding rows (none without y motion)
   static constexpr int WX = BX + 2;
   static constexpr int WY = BY + 2 * PY;
+  static constexpr int WPLANE = WY * WX;
   static constexpr int HW = NXF * WY;  // west (and east) ring entries
   static constexpr int HS = NYF * BX;  // south (and north) ring entries
   static constexpr int H = 2 * HW + 2 * HS;
   static constexpr int HPT = (H + NT - 1) / NT;
   static constexpr int PMAX = NYF > 0 ? 2 * BX + 2 * (BY - 2) : 2;  // lateral perimeter nodes
   static constexpr int NEXW = (PMAX + 31) / 32;                     // export warps
+  // stage row of one perimeter node: Q values padded so that the row is a
+  // whole, odd number of 16-byte units (vector stores, conflict-free loads)
+  static constexpr int VEC = 16 / int(sizeof(R));
+  static constexpr int QP = ((Q + VEC - 1) / VEC) % 2 == 1 ? (Q + VEC - 1) / VEC * VEC : ((Q + VEC - 1) / VEC + 1) * VEC;
   static constexpr size_t SLOT = size_t(Q) * BY * BX * sizeof(S);
-  static constexpr size_t WIN = size_t(NLAT) * WY * WX * sizeof(R);
-  static constexpr size_t STAGE = size_t(Q) * PMAX * sizeof(R);
+  static constexpr size_t WIN = size_t(NLAT) * WPLANE * sizeof(R);
+  static constexpr size_t STAGE = size_t(QP) * PMAX * sizeof(R);
   static constexpr size_t OFF_WIN = align128(NS * SLOT);
-  static constexpr size_t OFF_STAGE = OFF_WIN + align128(WIN);
+  static constexpr size_t OFF_STAGE = OFF_WIN + WB * align128(WIN);
   static constexpr size_t OFF_BAR = OFF_STAGE + align128(2 * STAGE);
   static constexpr size_t SMEM = OFF_BAR + align128(NS * sizeof(uint64_t));
   static_assert(BY == 1 || NYF > 0, "a 2D brick has one internal row");
   static_assert(PMAX <= NT, "perimeter larger than the CTA");
+  static_assert(WB == 1 || WB == 2, "one or two window buffers");
 };
 
 // index of the lateral perimeter node (tx, ty) of an active bxa x bya brick
@@ -154,12 +162,35 @@ __device__ __forceinline__ void perimeter_node(int p, int bxa, int bya, int& tx,
   }
 }
 
+// Faces of a brick through which a boundary node exports (bit flags).
+enum : unsigned { kFaceW = 1, kFaceE = 2, kFaceS = 4, kFaceN = 8, kFaceD = 16, kFaceU = 32 };
+
+// Shell offsets of one node, hoisted out of the per-direction stores: the
+// ia-th exported direction of a face lands at base + ia * stride.
+template <class R>
+struct ShellSpot {
+  R* base;
+  int64_t stride;
+};
+
+// Write the directions of one face: those whose component along `axis` is
+// `sign` (the populations leaving through that face).
+template <class L, class R, int axis, int sign>
+__device__ __forceinline__ void export_face(const Coef<R>& kc, ShellSpot<R> s) {
+  static_for<0, L::Q>([&](auto A_) {
+    constexpr int a = decltype(A_)::value;
+    if constexpr (comp<L>(axis, a) == sign) {
+      constexpr int ia = sub_index<L>(axis, sign, a);
+      s.base[ia * s.stride] = post<L, R, a>(kc);
+    }
+  });
+}
+
 // Collide the completed (rounded) state of one node once more and export the
 // populations that leave the brick through the flagged faces.
 template <class L, class S, class R, bool FORCE>
 __device__ __forceinline__ void export_node(const K1Args<R>& args, const R (&fin)[L::Q], int x, int y, int zd,
-                                            bool eW, bool eE, bool eS, bool eN, bool eD, bool eU, int bI, int bJ,
-                                            int bK) {
+                                            unsigned faces, int bI, int bJ, int bK) {
   constexpr int NXF = count_dirs<L>(0, 1), NYF = count_dirs<L>(1, 1), NZF = count_dirs<L>(2, 1);
   R fr[L::Q];
   static_for<0, L::Q>([&](auto A_) {
@@ -171,55 +202,54 @@ __device__ __forceinline__ void export_node(const K1Args<R>& args, const R (&fin
   Coef<R> kc;
   coeffs<L, R, FORCE>(m, args.ph, kc);
   R* shn = args.sh_next;
-  const int nx = args.nx, ny = args.ny, nz = args.nz;
-  static_for<0, L::Q>([&](auto A_) {
-    constexpr int a = decltype(A_)::value;
-    constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
-    const bool wx = (cx == -1 && eW) || (cx == 1 && eE);
-    const bool wy = (cy == -1 && eS) || (cy == 1 && eN);
-    const bool wz = (cz == -1 && eD) || (cz == 1 && eU);
-    if (wx || wy || wz) {
-      const R v = post<L, R, a>(kc);
-      if constexpr (cx != 0) {
-        if (wx) {
-          constexpr int side = cx == 1 ? 1 : 0;
-          constexpr int ia = sub_index<L>(0, cx, a);
-          shn[args.sx_off + ((int64_t(side) * args.nbx + bI) * NXF + ia) * int64_t(nz) * ny + int64_t(zd) * ny + y] = v;
-        }
-      }
-      if constexpr (cy != 0) {
-        if (wy) {
-          constexpr int side = cy == 1 ? 1 : 0;
-          constexpr int ia = sub_index<L>(1, cy, a);
-          shn[args.sy_off + ((int64_t(side) * args.nby + bJ) * NYF + ia) * int64_t(nz) * nx + int64_t(zd) * nx + x] = v;
-        }
-      }
-      if constexpr (cz != 0) {
-        if (wz) {
-          constexpr int side = cz == 1 ? 1 : 0;
-          constexpr int ia = sub_index<L>(2, cz, a);
-          shn[args.sz_off + ((int64_t(side) * args.nbz + bK) * NZF + ia) * int64_t(ny) * nx + int64_t(y) * nx + x] = v;
-        }
-      }
+  const int64_t nzy = int64_t(args.nz) * args.ny, nzx = int64_t(args.nz) * args.nx;
+  const int64_t nyx = int64_t(args.ny) * args.nx;
+  if (faces & (kFaceW | kFaceE)) {
+    // SX[side][I][ia][z][y]
+    const int64_t row = int64_t(zd) * args.ny + y;
+    if (faces & kFaceW)
+      export_face<L, R, 0, -1>(kc, {shn + args.sx_off + (int64_t(bI) * NXF) * nzy + row, nzy});
+    if (faces & kFaceE)
+      export_face<L, R, 0, 1>(kc, {shn + args.sx_off + ((int64_t(args.nbx) + bI) * NXF) * nzy + row, nzy});
+  }
+  if constexpr (NYF > 0) {
+    if (faces & (kFaceS | kFaceN)) {
+      // SY[side][J][ia][z][x]
+      const int64_t row = int64_t(zd) * args.nx + x;
+      if (faces & kFaceS)
+        export_face<L, R, 1, -1>(kc, {shn + args.sy_off + (int64_t(bJ) * NYF) * nzx + row, nzx});
+      if (faces & kFaceN)
+        export_face<L, R, 1, 1>(kc, {shn + args.sy_off + ((int64_t(args.nby) + bJ) * NYF) * nzx + row, nzx});
     }
-  });
+  }
+  if (faces & (kFaceD | kFaceU)) {
+    // SZ[side][K][ia][y][x]
+    const int64_t row = int64_t(y) * args.nx + x;
+    if (faces & kFaceD)
+      export_face<L, R, 2, -1>(kc, {shn + args.sz_off + (int64_t(bK) * NZF) * nyx + row, nyx});
+    if (faces & kFaceU)
+      export_face<L, R, 2, 1>(kc, {shn + args.sz_off + ((int64_t(args.nbz) + bK) * NZF) * nyx + row, nyx});
+  }
 }
 
-template <class L, class S, class R, int BX, int BY, int NS, bool FORCE>
+template <class L, class S, class R, int BX, int BY, int NS, int WB, bool FORCE>
 __global__ void __launch_bounds__(BX* BY, 1)
     k1_fused_step(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ K1Args<R> args) {
-  using Sh = K1Shape<L, S, R, BX, BY, NS>;
+  using Sh = K1Shape<L, S, R, BX, BY, NS, WB>;
+  static_assert(WB == 2, "the pipelined sweep needs two window buffers");
   constexpr int Q = L::Q;
   constexpr int NT = Sh::NT;
   constexpr int NXF = Sh::NXF, NYF = Sh::NYF, NZF = Sh::NZF;
-  constexpr int PY = Sh::PY, WX = Sh::WX, WY = Sh::WY;
+  constexpr int PY = Sh::PY, WX = Sh::WX, WPLANE = Sh::WPLANE;
   constexpr int HW = Sh::HW, HS = Sh::HS, H = Sh::H, HPT = Sh::HPT;
-  constexpr int PMAX = Sh::PMAX, NEXW = Sh::NEXW;
-  constexpr int WPLANE = WY * WX;
+  constexpr int PMAX = Sh::PMAX, NEXW = Sh::NEXW, QP = Sh::QP, VEC = Sh::VEC;
+  constexpr int WY = Sh::WY;
+  constexpr int WSTRIDE = int(align128(Sh::WIN) / sizeof(R));  // between window buffers
+  using Vec = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
 
   extern __shared__ __align__(128) unsigned char smem[];
   S* slots = reinterpret_cast<S*>(smem);
-  R* win = reinterpret_cast<R*>(smem + Sh::OFF_WIN);
+  R* win0 = reinterpret_cast<R*>(smem + Sh::OFF_WIN);
   R* stage = reinterpret_cast<R*>(smem + Sh::OFF_STAGE);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Sh::OFF_BAR);
 
@@ -339,24 +369,109 @@ __global__ void __launch_bounds__(BX* BY, 1)
     return false;
   };
 
-  R hreg[HPT];
-  auto halo_fetch = [&](int z) {
-    const int zw = (z + nz) % nz;
+  // ring values of two planes ahead in registers: ha = plane being produced,
+  // hb = the next one (loads in flight for about two planes).  The entry
+  // pointers walk up one plane per call; planes below 0 or above nz - 1 only
+  // occur for periodic z and wrap.
+  R ha[HPT], hb[HPT];
+  const R* hptr[HPT];
 #pragma unroll
-    for (int e = 0; e < HPT; ++e) hreg[e] = hval[e] ? shc[hbase[e] + int64_t(zw) * hzs[e]] : R(0);
+  for (int e = 0; e < HPT; ++e) hptr[e] = shc + hbase[e];
+  auto halo_fetch = [&](R(&dst)[HPT], int z) {
+    const bool ok = z <= z1 && plane_needed(z);
+    const int zw = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+#pragma unroll
+    for (int e = 0; e < HPT; ++e) dst[e] = (ok && hval[e]) ? hptr[e][int64_t(zw) * hzs[e]] : R(0);
   };
-  if (plane_needed(z0 - 1)) halo_fetch(z0 - 1);
+  halo_fetch(ha, z0 - 1);
+  halo_fetch(hb, z0);
 
   // perimeter (lateral boundary) slot of this node, and export-warp work
   const int pidx = active ? perimeter_index<NYF>(tx, ty, bxa, bya) : -1;
   const int pcount = perimeter_count<NYF>(bxa, bya);
   const bool any_lateral_export = nbW || nbE || (NYF > 0 && (nbS || nbN));
+  const bool exp_warp = any_lateral_export && warp < NEXW;
 
   // this thread's own cell in the window (interior of the padding ring)
   const int wbase = (ty + PY) * WX + (tx + 1);
 
+  // export of the staged lateral perimeter of plane zx (whole warps)
+  auto export_staged = [&](int zx) {
+    if (exp_warp && zx >= z0 && zx < z1) {
+      const int p = warp * 32 + lane;
+      if (p < pcount) {
+        int ptx, pty;
+        perimeter_node<NYF>(p, bxa, bya, ptx, pty);
+        const Vec* st = reinterpret_cast<const Vec*>(stage + (zx & 1) * (QP * PMAX) + p * QP);
+        R fin[QP];
+#pragma unroll
+        for (int v = 0; v < QP / VEC; ++v) *reinterpret_cast<Vec*>(&fin[v * VEC]) = st[v];
+        R fq[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) fq[a] = fin[a];
+        const unsigned faces = (ptx == 0 && nbW ? kFaceW : 0u) | (ptx == bxa - 1 && nbE ? kFaceE : 0u) |
+                               (NYF > 0 && pty == 0 && nbS ? kFaceS : 0u) |
+                               (NYF > 0 && pty == bya - 1 && nbN ? kFaceN : 0u);
+        export_node<L, S, R, FORCE>(args, fq, x0 + ptx, y0 + pty, zx, faces, bI, bJ, bK);
+      }
+    }
+  };
+
+  // Produce the window of plane c: collide a real plane (TMA slot) or copy a
+  // virtual plane from the shell; the populations that do not move laterally
+  // stay in onl (rest, +z, -z).  Returns false if the TMA wait timed out.
+  auto produce = [&](int c, R* win, R (&onl)[3]) -> bool {
+    const bool real = c >= z0 && c < z1;
+    if (real) {
+      const int k = c - z0;
+      const int slot = k % NS;
+      if (!mbar_wait_bounded(&bars[slot], (k / NS) & 1, kWaitLimitNs)) return false;
+      if (active) {
+        const S* sl = slots + size_t(slot) * Q * BY * BX + ty * BX + tx;
+        R fl[Q], own[Q];
+        static_for<0, Q>([&](auto A_) {
+          constexpr int a = decltype(A_)::value;
+          fl[a] = load_as<S, R>(sl[a * BY * BX]);
+        });
+        collide<L, R, FORCE>(fl, args.ph, own);
+        static_for<0, Q>([&](auto A_) {
+          constexpr int a = decltype(A_)::value;
+          if constexpr (is_lateral<L>(a)) win[lat_index<L>(a) * WPLANE + wbase] = own[a];
+          else onl[a == 0 ? 0 : (L::cz(a) == 1 ? 1 : 2)] = own[a];
+        });
+      }
+    } else if (plane_needed(c) && active) {
+      // virtual plane just outside the brick: the neighbouring brick's export
+      const bool low = (c == z0 - 1);
+      const int side = low ? 1 : 0;
+      const int bb = low ? bKd : bKu;
+      const int64_t base = args.sz_off + (int64_t(side) * nbz + bb) * NZF * int64_t(ny) * nx + int64_t(y) * nx + x;
+      onl[0] = onl[1] = onl[2] = R(0);
+      static_for<0, Q>([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        constexpr int cz = L::cz(a);
+        if constexpr (cz != 0) {
+          if ((cz == 1) == low) {
+            constexpr int iz = sub_index<L>(2, cz, a);
+            const R v = shc[base + int64_t(iz) * ny * nx];
+            if constexpr (is_lateral<L>(a)) win[lat_index<L>(a) * WPLANE + wbase] = v;
+            else onl[cz == 1 ? 1 : 2] = v;
+          }
+        }
+      });
+    }
+    if (plane_needed(c)) {
+      // only valid entries: an invalid north/south entry of a ragged brick
+      // would alias the east ring's corner cell of a diagonal direction
+#pragma unroll
+      for (int e = 0; e < HPT; ++e)
+        if (hval[e]) win[hsm[e]] = ha[e];
+    }
+    return true;
+  };
+
   // three destination planes of gathered populations
-  R G0[Q], G1[Q], G2[Q];  // planes z-1, z, z+1
+  R G0[Q], G1[Q], G2[Q];  // planes g-1, g, g+1 of the plane g being gathered
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
     G0[a] = R(0);
@@ -371,95 +486,57 @@ __global__ void __launch_bounds__(BX* BY, 1)
 #pragma unroll
   for (int i = 0; i < NDN; ++i) bdn[i] = R(0);
 
-  const int n_it = (z1 - z0) + 2;
-  for (int it = 0; it < n_it; ++it) {
-    const int z = z0 - 1 + it;
-    const bool real = z >= z0 && z < z1;
-    const bool need = plane_needed(z);
-    const int k = z - z0;
-    const int slot = real ? (k % NS) : 0;
-    bool timeout = false;
-    R own[Q];  // this node's collided populations (real planes)
-
-    // ---------------------------------------------- phase 1: window of plane z
-    if (real) {
-      if (!mbar_wait_bounded(&bars[slot], (k / NS) & 1, kWaitLimitNs)) timeout = true;
-      if (!timeout && active) {
-        const S* sl = slots + size_t(slot) * Q * BY * BX + ty * BX + tx;
-        R fl[Q];
-        static_for<0, Q>([&](auto A_) {
-          constexpr int a = decltype(A_)::value;
-          fl[a] = load_as<S, R>(sl[a * BY * BX]);
-        });
-        collide<L, R, FORCE>(fl, args.ph, own);
-        static_for<0, Q>([&](auto A_) {
-          constexpr int a = decltype(A_)::value;
-          if constexpr (is_lateral<L>(a)) win[lat_index<L>(a) * WPLANE + wbase] = own[a];
-        });
-      }
-    } else if (need && active) {
-      // virtual plane just outside the brick: the neighbouring brick's export
-      const bool low = (z == z0 - 1);
-      const int side = low ? 1 : 0;
-      const int bb = low ? bKd : bKu;
-      const int64_t base = args.sz_off + (int64_t(side) * nbz + bb) * NZF * int64_t(ny) * nx + int64_t(y) * nx + x;
-      static_for<0, Q>([&](auto A_) {
-        constexpr int a = decltype(A_)::value;
-        constexpr int cz = L::cz(a);
-        own[a] = R(0);
-        if constexpr (cz != 0) {
-          if ((cz == 1) == low) {
-            constexpr int iz = sub_index<L>(2, cz, a);
-            const R v = shc[base + int64_t(iz) * ny * nx];
-            if constexpr (is_lateral<L>(a)) win[lat_index<L>(a) * WPLANE + wbase] = v;
-            else own[a] = v;
-          }
-        }
-      });
+  auto abort_cta = [&](int k) {
+    if (tid == 0) {
+      atomicExch(args.status, LB_E_TIMEOUT);
+      // drain this CTA's own copies still in flight (bounded)
+      for (int kk = (k < 0 ? 0 : k); kk < issued; ++kk) mbar_wait_bounded(&bars[kk % NS], (kk / NS) & 1, kWaitLimitNs);
     }
-    if (need) {
-      // only valid entries: an invalid north/south entry of a ragged brick
-      // would alias the east ring's corner cell of a diagonal direction
-#pragma unroll
-      for (int e = 0; e < HPT; ++e)
-        if (hval[e]) win[hsm[e]] = hreg[e];
-    }
-    if (z + 1 <= z1 && plane_needed(z + 1)) halo_fetch(z + 1);
+  };
 
-    if (__syncthreads_or(timeout)) {
-      if (tid == 0) {
-        atomicExch(args.status, LB_E_TIMEOUT);
-        // drain this CTA's own copies still in flight (bounded)
-        for (int kk = (k < 0 ? 0 : k); kk < issued; ++kk)
-          mbar_wait_bounded(&bars[kk % NS], (kk / NS) & 1, kWaitLimitNs);
-      }
+  // ------------------------------------------------ prologue: plane z0 - 1
+  R onl_g[3] = {R(0), R(0), R(0)};  // non-lateral populations of the gathered plane
+  {
+    bool ok = produce(z0 - 1, win0 + ((z0 - 1) & 1) * WSTRIDE, onl_g);
+    if (__syncthreads_or(!ok)) {
+      abort_cta(0);
       return;
     }
+  }
+#pragma unroll
+  for (int e = 0; e < HPT; ++e) ha[e] = hb[e];
+  halo_fetch(hb, z0 + 1);
 
-    // refill the slot just consumed with plane z + NS
-    if (real && tid == 0) {
-      const int zz = z + NS;
-      if (zz < z1) {
-        mbar_arrive_expect_tx(&bars[slot], static_cast<uint32_t>(Sh::SLOT));
-        tma_load_4d(slots + size_t(slot) * Q * BY * BX, &tmap, x0, y0, zz, 0, &bars[slot]);
-        ++issued;
-      }
-    }
+  // ------------------------------------------------ sweep: gather plane g,
+  // produce plane g + 1 in the same barrier interval (independent work)
+  for (int g = z0 - 1; g <= z1; ++g) {
+    const int c = g + 1;
+    R* win_g = win0 + (g & 1) * WSTRIDE;
+    R* win_c = win0 + (c & 1) * WSTRIDE;
+    const bool real_g = g >= z0 && g < z1;
+    const bool need_g = plane_needed(g);
 
-    // ---------------------------------------------- phase 2: gather (no branches)
-    if (active && need) {
+    R onl_c[3] = {R(0), R(0), R(0)};
+    bool ok = true;
+    if (c <= z1) ok = produce(c, win_c, onl_c);
+
+    // gather plane g (window complete since the previous barrier)
+    if (active && need_g) {
       static_for<0, Q>([&](auto A_) {
         constexpr int a = decltype(A_)::value;
         constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
         R v;
-        if constexpr (is_lateral<L>(a)) v = win[lat_index<L>(a) * WPLANE + wbase - cy * WX - cx];
-        else v = own[a];
+        if constexpr (is_lateral<L>(a)) v = win_g[lat_index<L>(a) * WPLANE + wbase - cy * WX - cx];
+        else v = onl_g[a == 0 ? 0 : (cz == 1 ? 1 : 2)];
         if constexpr (cz == -1) G0[a] = v;
         if constexpr (cz == 0) G1[a] = v;
         if constexpr (cz == 1) G2[a] = v;
       });
     }
-    // z-descending bounce-backs of plane z - 1, saved one plane ago
+    // exports of plane g - 2 (staged one iteration ago)
+    export_staged(g - 2);
+
+    // z-descending bounce-backs of plane g - 1, saved one plane ago
     if (bdn_mask) {
       static_for<0, Q>([&](auto A_) {
         constexpr int a = decltype(A_)::value;
@@ -470,9 +547,9 @@ __global__ void __launch_bounds__(BX* BY, 1)
       });
       bdn_mask = 0;
     }
-    // halfway bounce-back for destination plane z (threads next to a wall)
-    if (real && active && (xy_wall || (z_walls && (z == 0 || z == nz - 1)))) {
-      const bool bzlo = z_walls && z == 0, bzhi = z_walls && z == nz - 1;
+    // halfway bounce-back for destination plane g (threads next to a wall)
+    if (real_g && active && (xy_wall || (z_walls && (g == 0 || g == nz - 1)))) {
+      const bool bzlo = z_walls && g == 0, bzhi = z_walls && g == nz - 1;
       static_for<0, Q>([&](auto A_) {
         constexpr int a = decltype(A_)::value;
         constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
@@ -486,8 +563,8 @@ __global__ void __launch_bounds__(BX* BY, 1)
         if (cb != 0) {
           constexpr int oa = L::opp(a);
           R back;
-          if constexpr (is_lateral<L>(oa)) back = win[lat_index<L>(oa) * WPLANE + wbase];
-          else back = own[oa];
+          if constexpr (is_lateral<L>(oa)) back = win_g[lat_index<L>(oa) * WPLANE + wbase];
+          else back = onl_g[oa == 0 ? 0 : (L::cz(oa) == 1 ? 1 : 2)];
           const R v = back + args.bb[a][cb];
           if constexpr (cz == -1) {
             constexpr int i = sub_index<L>(2, -1, a);
@@ -500,68 +577,61 @@ __global__ void __launch_bounds__(BX* BY, 1)
       });
     }
 
-    // ---------------------------------------------- exports of plane z - 2
-    const int zx = z - 2;  // staged one iteration ago
-    if (any_lateral_export && warp < NEXW && zx >= z0 && zx < z1) {
-      const int p = warp * 32 + lane;
-      if (p < pcount) {
-        int ptx, pty;
-        perimeter_node<NYF>(p, bxa, bya, ptx, pty);
-        const R* st = stage + (zx & 1) * (Q * PMAX) + p;
-        R fin[Q];
-        static_for<0, Q>([&](auto A_) {
-          constexpr int a = decltype(A_)::value;
-          fin[a] = st[a * PMAX];
-        });
-        export_node<L, S, R, FORCE>(args, fin, x0 + ptx, y0 + pty, zx, ptx == 0 && nbW, ptx == bxa - 1 && nbE,
-                                    pty == 0 && nbS, pty == bya - 1 && nbN, false, false, bI, bJ, bK);
-      }
-    }
-
-    // ---------------------------------------------- plane z - 1 is complete
-    const int zd = z - 1;
+    // plane g - 1 is complete: store, stage its perimeter, export along z
+    const int zd = g - 1;
     if (active && zd >= z0 && zd < z1) {
-      const int64_t o = x + args.pitch * (y + int64_t(ny) * zd);
+      S* p = fglob + (x + args.pitch * (y + int64_t(ny) * zd));
       static_for<0, Q>([&](auto A_) {
         constexpr int a = decltype(A_)::value;
-        fglob[a * args.vol + o] = store_as<S, R>(G0[a]);
+        *p = store_as<S, R>(G0[a]);
+        p += args.vol;
       });
       if (pidx >= 0 && any_lateral_export) {
-        R* st = stage + (zd & 1) * (Q * PMAX) + pidx;
-        static_for<0, Q>([&](auto A_) {
-          constexpr int a = decltype(A_)::value;
-          st[a * PMAX] = G0[a];
-        });
+        Vec* st = reinterpret_cast<Vec*>(stage + (zd & 1) * (QP * PMAX) + pidx * QP);
+#pragma unroll
+        for (int v = 0; v < QP / VEC; ++v) {
+          R tmp[VEC];
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) tmp[j] = (v * VEC + j < Q) ? G0[(v * VEC + j) < Q ? v * VEC + j : 0] : R(0);
+          st[v] = *reinterpret_cast<const Vec*>(tmp);
+        }
       }
       const bool eD = zd == z0 && nbD, eU = zd == z1 - 1 && nbU;
-      if (eD || eU) export_node<L, S, R, FORCE>(args, G0, x, y, zd, false, false, false, false, eD, eU, bI, bJ, bK);
+      if (eD || eU) export_node<L, S, R, FORCE>(args, G0, x, y, zd, (eD ? kFaceD : 0u) | (eU ? kFaceU : 0u), bI, bJ, bK);
     }
-    // rotate the destination planes
+
+    // ring values move up one plane; start the loads two planes ahead
+#pragma unroll
+    for (int e = 0; e < HPT; ++e) ha[e] = hb[e];
+    halo_fetch(hb, c + 2);
+
+    // rotate: plane g's partial set becomes the "previous" plane
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
       G0[a] = G1[a];
       G1[a] = G2[a];
     }
-    __syncthreads();
-  }
+    onl_g[0] = onl_c[0];
+    onl_g[1] = onl_c[1];
+    onl_g[2] = onl_c[2];
 
-  // exports of the last plane (staged in the final iteration)
-  const int zx = z1 - 1;
-  if (any_lateral_export && warp < NEXW && zx >= z0) {
-    const int p = warp * 32 + lane;
-    if (p < pcount) {
-      int ptx, pty;
-      perimeter_node<NYF>(p, bxa, bya, ptx, pty);
-      const R* st = stage + (zx & 1) * (Q * PMAX) + p;
-      R fin[Q];
-      static_for<0, Q>([&](auto A_) {
-        constexpr int a = decltype(A_)::value;
-        fin[a] = st[a * PMAX];
-      });
-      export_node<L, S, R, FORCE>(args, fin, x0 + ptx, y0 + pty, zx, ptx == 0 && nbW, ptx == bxa - 1 && nbE,
-                                  pty == 0 && nbS, pty == bya - 1 && nbN, false, false, bI, bJ, bK);
+    // the only barrier of the iteration: plane c's window is complete and
+    // every thread has left plane g's buffers, which plane c + 1 reuses
+    if (__syncthreads_or(!ok)) {
+      abort_cta(c - z0);
+      return;
+    }
+    // refill the slot consumed by plane c with plane c + NS
+    if (tid == 0 && c >= z0 && c < z1 && c + NS < z1) {
+      const int slot = (c - z0) % NS;
+      mbar_arrive_expect_tx(&bars[slot], static_cast<uint32_t>(Sh::SLOT));
+      tma_load_4d(slots + size_t(slot) * Q * BY * BX, &tmap, x0, y0, c + NS, 0, &bars[slot]);
+      ++issued;
     }
   }
+
+  // exports of the last two planes
+  export_staged(z1 - 1);
 }
 
 // Shell bootstrap: collide every brick-boundary node of the current state and
@@ -592,7 +662,9 @@ __global__ void __launch_bounds__(256) k1_bootstrap(const __grid_constant__ K1Ar
       constexpr int a = decltype(A_)::value;
       fr[a] = load_as<S, R>(fg[a * args.vol + o]);
     });
-    export_node<L, S, R, FORCE>(args, fr, x, y, z, eW, eE, eS, eN, eD, eU, bI, bJ, bK);
+    const unsigned faces = (eW ? kFaceW : 0u) | (eE ? kFaceE : 0u) | (eS ? kFaceS : 0u) | (eN ? kFaceN : 0u) |
+                           (eD ? kFaceD : 0u) | (eU ? kFaceU : 0u);
+    export_node<L, S, R, FORCE>(args, fr, x, y, z, faces, bI, bJ, bK);
   }
 }
 

@@ -1,6 +1,7 @@
 // lb_k1_plan.cu -- brick decomposition of the fused step: picks a compiled
 // brick shape, the sweep length bz, and lays out the shell buffers.
 #include <cstdio>
+#include <cstdlib>
 
 #include "lb_k1_launch.cuh"
 
@@ -13,7 +14,9 @@ extern const int k1_n_variants_d3q19;
 extern const K1Variant k1_variants_d3q27[];
 extern const int k1_n_variants_d3q27;
 
-static const K1Variant* find_variant(int lattice, int storage, int bx, int by) {
+// The first compiled shape that matches (lattice, storage, bx, by, ns, wb);
+// zero fields match anything.
+static const K1Variant* find_variant(int lattice, int storage, int bx, int by, int ns, int wb) {
   const K1Variant* list = nullptr;
   int n = 0;
   switch (lattice) {
@@ -27,9 +30,20 @@ static const K1Variant* find_variant(int lattice, int storage, int bx, int by) {
     if (v.storage != storage) continue;
     if (bx > 0 && v.bx != bx) continue;
     if (by > 0 && v.by != by) continue;
+    if (ns > 0 && v.ns != ns) continue;
+    if (wb > 0 && v.wb != wb) continue;
     return &v;
   }
   return nullptr;
+}
+
+// Optional pipeline request from the environment, "NS,WB" (TMA slots, window
+// buffers), used to compare the compiled alternatives of a brick shape.
+static void pipeline_request(int* ns, int* wb) {
+  *ns = 0;
+  *wb = 0;
+  const char* e = std::getenv("LB_FUSED_PIPELINE");
+  if (e) std::sscanf(e, "%d,%d", ns, wb);
 }
 
 static int sm_count() {
@@ -65,12 +79,15 @@ static int choose_bz(int nz, int columns, int slots, int sms) {
 bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPlan* plan) {
   const int rbx = tile_req ? tile_req[0] : 0;
   const int rby = tile_req ? tile_req[1] : 0;
-  const K1Variant* v = find_variant(g.lattice, storage, rbx, rby);
+  int rns, rwb;
+  pipeline_request(&rns, &rwb);
+  const K1Variant* v = find_variant(g.lattice, storage, rbx, rby, rns, rwb);
   if (!v) return false;
   FusedPlan p{};
   p.bx = v->bx;
   p.by = v->by;
   p.slots = v->ns;
+  p.wbuf = v->wb;
   p.smem_bytes = v->smem;
   p.nbx = (g.nx + p.bx - 1) / p.bx;
   p.nby = (g.ny + p.by - 1) / p.by;
@@ -97,7 +114,7 @@ bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPla
 }
 
 static const K1Variant* ctx_variant(lb_ctx* ctx) {
-  return find_variant(ctx->lattice, ctx->storage, ctx->plan.bx, ctx->plan.by);
+  return find_variant(ctx->lattice, ctx->storage, ctx->plan.bx, ctx->plan.by, ctx->plan.slots, ctx->plan.wbuf);
 }
 
 cudaError_t k1_configure(lb_ctx* ctx) {
