@@ -35,6 +35,7 @@ struct FusedPlan {
   int64_t parity_elems;
   int slots;               // TMA pipeline depth
   int wbuf;                // shared window buffers (2: one barrier per plane)
+  int xwarps;              // dedicated export warps (0: node-owning warps export)
   size_t smem_bytes;
 };
 

@@ -90,10 +90,11 @@ LB_HD constexpr int dir_of_sub(int axis, int sign, int ia) {
   return -1;
 }
 
-template <class L, class S, class R, int BX, int BY, int NS, int WB>
+template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW>
 struct K1Shape {
   static constexpr int Q = L::Q;
-  static constexpr int NT = BX * BY;
+  static constexpr int NTM = BX * BY;        // threads that own a node
+  static constexpr int NT = NTM + 32 * NXW;  // + dedicated export warps
   static constexpr int NXF = count_dirs<L>(0, 1);
   static constexpr int NYF = count_dirs<L>(1, 1);
   static constexpr int NZF = count_dirs<L>(2, 1);
@@ -105,9 +106,10 @@ struct K1Shape {
   static constexpr int HW = NXF * WY;  // west (and east) ring entries
   static constexpr int HS = NYF * BX;  // south (and north) ring entries
   static constexpr int H = 2 * HW + 2 * HS;
-  static constexpr int HPT = (H + NT - 1) / NT;
+  static constexpr int HPT = (H + NTM - 1) / NTM;
   static constexpr int PMAX = NYF > 0 ? 2 * BX + 2 * (BY - 2) : 2;  // lateral perimeter nodes
-  static constexpr int NEXW = (PMAX + 31) / 32;                     // export warps
+  // export warps: the first NEXW node-owning warps, or NXW dedicated ones
+  static constexpr int NEXW = NXW > 0 ? NXW : (PMAX + 31) / 32;
   // stage row of one perimeter node: Q values padded so that the row is a
   // whole, odd number of 16-byte units (vector stores, conflict-free loads)
   static constexpr int VEC = 16 / int(sizeof(R));
@@ -117,10 +119,11 @@ struct K1Shape {
   static constexpr size_t STAGE = size_t(QP) * PMAX * sizeof(R);
   static constexpr size_t OFF_WIN = align128(NS * SLOT);
   static constexpr size_t OFF_STAGE = OFF_WIN + WB * align128(WIN);
-  static constexpr size_t OFF_BAR = OFF_STAGE + align128(2 * STAGE);
+  static constexpr size_t OFF_DESC = OFF_STAGE + align128(2 * STAGE);
+  static constexpr size_t OFF_BAR = OFF_DESC + align128(size_t(PMAX) * 24);
   static constexpr size_t SMEM = OFF_BAR + align128(NS * sizeof(uint64_t));
   static_assert(BY == 1 || NYF > 0, "a 2D brick has one internal row");
-  static_assert(PMAX <= NT, "perimeter larger than the CTA");
+  static_assert(NXW > 0 || PMAX <= NTM, "perimeter larger than the CTA");
   static_assert(WB == 1 || WB == 2, "one or two window buffers");
 };
 
@@ -232,13 +235,36 @@ __device__ __forceinline__ void export_node(const K1Args<R>& args, const R (&fin
   }
 }
 
-template <class L, class S, class R, int BX, int BY, int NS, int WB, bool FORCE>
-__global__ void __launch_bounds__(BX* BY, 1)
+// Export of one lateral perimeter node whose shell locations were resolved
+// once per brick: pw / ps point at the node's low-side x-face / y-face record
+// of this plane; the high-side records lie dxe / dyn elements further.
+template <class L, class S, class R, bool FORCE>
+__device__ __forceinline__ void export_lateral(const K1Args<R>& args, const R (&fin)[L::Q], unsigned faces, R* pw,
+                                               R* ps, int64_t dxe, int64_t dyn, int64_t sxs, int64_t sys) {
+  R fr[L::Q];
+  static_for<0, L::Q>([&](auto A_) {
+    constexpr int a = decltype(A_)::value;
+    fr[a] = round_to_storage<S, R>(fin[a]);
+  });
+  Mom<R> m;
+  moments<L, R, FORCE>(fr, args.ph, m);
+  Coef<R> kc;
+  coeffs<L, R, FORCE>(m, args.ph, kc);
+  if (faces & kFaceW) export_face<L, R, 0, -1>(kc, {pw, sxs});
+  if (faces & kFaceE) export_face<L, R, 0, 1>(kc, {pw + dxe, sxs});
+  if constexpr (count_dirs<L>(1, 1) > 0) {
+    if (faces & kFaceS) export_face<L, R, 1, -1>(kc, {ps, sys});
+    if (faces & kFaceN) export_face<L, R, 1, 1>(kc, {ps + dyn, sys});
+  }
+}
+
+template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE>
+__global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
     k1_fused_step(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ K1Args<R> args) {
-  using Sh = K1Shape<L, S, R, BX, BY, NS, WB>;
+  using Sh = K1Shape<L, S, R, BX, BY, NS, WB, NXW>;
   static_assert(WB == 2, "the pipelined sweep needs two window buffers");
   constexpr int Q = L::Q;
-  constexpr int NT = Sh::NT;
+  constexpr int NTM = Sh::NTM;
   constexpr int NXF = Sh::NXF, NYF = Sh::NYF, NZF = Sh::NZF;
   constexpr int PY = Sh::PY, WX = Sh::WX, WPLANE = Sh::WPLANE;
   constexpr int HW = Sh::HW, HS = Sh::HS, H = Sh::H, HPT = Sh::HPT;
@@ -252,10 +278,15 @@ __global__ void __launch_bounds__(BX* BY, 1)
   R* win0 = reinterpret_cast<R*>(smem + Sh::OFF_WIN);
   R* stage = reinterpret_cast<R*>(smem + Sh::OFF_STAGE);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Sh::OFF_BAR);
+  // per perimeter node: shell offsets (plane 0) of its x-face and y-face
+  // records, and its face flags
+  int64_t* desc_off = reinterpret_cast<int64_t*>(smem + Sh::OFF_DESC);
+  unsigned* desc_faces = reinterpret_cast<unsigned*>(smem + Sh::OFF_DESC + size_t(PMAX) * 16);
 
   const int tid = threadIdx.x;
+  const bool is_main = tid < NTM;  // owns node (tx, ty); the rest only export
   const int tx = tid % BX;
-  const int ty = tid / BX;
+  const int ty = is_main ? tid / BX : BY;
   const int warp = tid / 32, lane = tid % 32;
   const int nx = args.nx, ny = args.ny, nz = args.nz;
   const int nbx = args.nbx, nby = args.nby, nbz = args.nbz;
@@ -317,7 +348,7 @@ __global__ void __launch_bounds__(BX* BY, 1)
   bool hval[HPT];
 #pragma unroll
   for (int e = 0; e < HPT; ++e) {
-    const int h = tid + e * NT;
+    const int h = is_main ? tid + e * NTM : H;
     hval[e] = false;
     hbase[e] = 0;
     hzs[e] = 1;
@@ -390,18 +421,37 @@ __global__ void __launch_bounds__(BX* BY, 1)
   const int pidx = active ? perimeter_index<NYF>(tx, ty, bxa, bya) : -1;
   const int pcount = perimeter_count<NYF>(bxa, bya);
   const bool any_lateral_export = nbW || nbE || (NYF > 0 && (nbS || nbN));
-  const bool exp_warp = any_lateral_export && warp < NEXW;
+  const bool exp_warp = any_lateral_export && (NXW > 0 ? !is_main : warp < NEXW);
+  const int exp_lane = NXW > 0 ? tid - NTM : warp * 32 + lane;  // first perimeter node of this lane
 
   // this thread's own cell in the window (interior of the padding ring)
   const int wbase = (ty + PY) * WX + (tx + 1);
 
   // export of the staged lateral perimeter of plane zx (whole warps)
+  // resolve each perimeter node's shell records once per brick
+  const int64_t nzy = int64_t(nz) * ny, nzx = int64_t(nz) * nx;
+  if (exp_warp) {
+#pragma unroll 1
+    for (int p = exp_lane; p < pcount; p += 32 * Sh::NEXW) {
+      int ptx, pty;
+      perimeter_node<NYF>(p, bxa, bya, ptx, pty);
+      const unsigned faces = (ptx == 0 && nbW ? kFaceW : 0u) | (ptx == bxa - 1 && nbE ? kFaceE : 0u) |
+                             (NYF > 0 && pty == 0 && nbS ? kFaceS : 0u) |
+                             (NYF > 0 && pty == bya - 1 && nbN ? kFaceN : 0u);
+      // SX[side][I][ia][z][y], SY[side][J][ia][z][x]; side 0 here, side 1 is
+      // a brick-uniform distance further (a node may export through both)
+      desc_off[2 * p] = args.sx_off + (int64_t(bI) * NXF) * nzy + (y0 + pty);
+      desc_off[2 * p + 1] = NYF > 0 ? args.sy_off + (int64_t(bJ) * NYF) * nzx + (x0 + ptx) : 0;
+      desc_faces[p] = faces;
+    }
+  }
+  // (the first barrier of the sweep orders these writes before their use)
+
   auto export_staged = [&](int zx) {
     if (exp_warp && zx >= z0 && zx < z1) {
-      const int p = warp * 32 + lane;
-      if (p < pcount) {
-        int ptx, pty;
-        perimeter_node<NYF>(p, bxa, bya, ptx, pty);
+      R* shn = args.sh_next;
+#pragma unroll 1
+      for (int p = exp_lane; p < pcount; p += 32 * Sh::NEXW) {
         const Vec* st = reinterpret_cast<const Vec*>(stage + (zx & 1) * (QP * PMAX) + p * QP);
         R fin[QP];
 #pragma unroll
@@ -409,10 +459,9 @@ __global__ void __launch_bounds__(BX* BY, 1)
         R fq[Q];
 #pragma unroll
         for (int a = 0; a < Q; ++a) fq[a] = fin[a];
-        const unsigned faces = (ptx == 0 && nbW ? kFaceW : 0u) | (ptx == bxa - 1 && nbE ? kFaceE : 0u) |
-                               (NYF > 0 && pty == 0 && nbS ? kFaceS : 0u) |
-                               (NYF > 0 && pty == bya - 1 && nbN ? kFaceN : 0u);
-        export_node<L, S, R, FORCE>(args, fq, x0 + ptx, y0 + pty, zx, faces, bI, bJ, bK);
+        export_lateral<L, S, R, FORCE>(args, fq, desc_faces[p], shn + desc_off[2 * p] + int64_t(zx) * ny,
+                                       shn + desc_off[2 * p + 1] + int64_t(zx) * nx, int64_t(nbx) * NXF * nzy,
+                                       int64_t(nby) * NYF * nzx, nzy, nzx);
       }
     }
   };
@@ -421,6 +470,7 @@ __global__ void __launch_bounds__(BX* BY, 1)
   // virtual plane from the shell; the populations that do not move laterally
   // stay in onl (rest, +z, -z).  Returns false if the TMA wait timed out.
   auto produce = [&](int c, R* win, R (&onl)[3]) -> bool {
+    if (!is_main) return true;
     const bool real = c >= z0 && c < z1;
     if (real) {
       const int k = c - z0;

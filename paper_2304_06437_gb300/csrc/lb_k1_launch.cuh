@@ -7,7 +7,7 @@
 namespace lbgb {
 
 struct K1Variant {
-  int lattice, storage, bx, by, ns, wb;
+  int lattice, storage, bx, by, ns, wb, nxw;
   size_t smem;
   cudaError_t (*configure)();
   cudaError_t (*step)(lb_ctx*);
@@ -43,15 +43,15 @@ K1Args<R> k1_make_args(lb_ctx* ctx, int cur_parity, int next_parity) {
   return a;
 }
 
-template <class L, class S, class R, int BX, int BY, int NS, int WB>
+template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW>
 struct K1Impl {
-  using Sh = K1Shape<L, S, R, BX, BY, NS, WB>;
+  using Sh = K1Shape<L, S, R, BX, BY, NS, WB, NXW>;
 
   static cudaError_t configure() {
-    cudaError_t e = cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, false>,
+    cudaError_t e = cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::SMEM));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, true>,
+    return cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::SMEM));
   }
 
@@ -60,9 +60,9 @@ struct K1Impl {
     make_bounce_terms<L, R>(ctx->g, a.bb);
     const int grid = ctx->plan.nbx * ctx->plan.nby * ctx->plan.nbz;
     if (ctx->g.has_force)
-      k1_fused_step<L, S, R, BX, BY, NS, WB, true><<<grid, BX * BY, Sh::SMEM, ctx->stream>>>(ctx->tmap, a);
+      k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true><<<grid, Sh::NT, Sh::SMEM, ctx->stream>>>(ctx->tmap, a);
     else
-      k1_fused_step<L, S, R, BX, BY, NS, WB, false><<<grid, BX * BY, Sh::SMEM, ctx->stream>>>(ctx->tmap, a);
+      k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false><<<grid, Sh::NT, Sh::SMEM, ctx->stream>>>(ctx->tmap, a);
     return cudaGetLastError();
   }
 
@@ -80,7 +80,7 @@ struct K1Impl {
   }
 
   static constexpr K1Variant variant(int lattice, int storage) {
-    return K1Variant{lattice, storage, BX, BY, NS, WB, Sh::SMEM, &configure, &step, &bootstrap};
+    return K1Variant{lattice, storage, BX, BY, NS, WB, NXW, Sh::SMEM, &configure, &step, &bootstrap};
   }
 };
 

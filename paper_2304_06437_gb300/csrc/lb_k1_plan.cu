@@ -14,9 +14,9 @@ extern const int k1_n_variants_d3q19;
 extern const K1Variant k1_variants_d3q27[];
 extern const int k1_n_variants_d3q27;
 
-// The first compiled shape that matches (lattice, storage, bx, by, ns, wb);
-// zero fields match anything.
-static const K1Variant* find_variant(int lattice, int storage, int bx, int by, int ns, int wb) {
+// The first compiled shape that matches (lattice, storage, bx, by, ns, wb,
+// nxw); zero fields (negative nxw) match anything.
+static const K1Variant* find_variant(int lattice, int storage, int bx, int by, int ns, int wb, int nxw) {
   const K1Variant* list = nullptr;
   int n = 0;
   switch (lattice) {
@@ -32,18 +32,21 @@ static const K1Variant* find_variant(int lattice, int storage, int bx, int by, i
     if (by > 0 && v.by != by) continue;
     if (ns > 0 && v.ns != ns) continue;
     if (wb > 0 && v.wb != wb) continue;
+    if (nxw >= 0 && v.nxw != nxw) continue;
     return &v;
   }
   return nullptr;
 }
 
-// Optional pipeline request from the environment, "NS,WB" (TMA slots, window
-// buffers), used to compare the compiled alternatives of a brick shape.
-static void pipeline_request(int* ns, int* wb) {
+// Optional pipeline request from the environment, "NS,WB[,NXW]" (TMA slots,
+// window buffers, dedicated export warps), used to compare the compiled
+// alternatives of a brick shape.
+static void pipeline_request(int* ns, int* wb, int* nxw) {
   *ns = 0;
   *wb = 0;
+  *nxw = -1;
   const char* e = std::getenv("LB_FUSED_PIPELINE");
-  if (e) std::sscanf(e, "%d,%d", ns, wb);
+  if (e) std::sscanf(e, "%d,%d,%d", ns, wb, nxw);
 }
 
 static int sm_count() {
@@ -79,15 +82,16 @@ static int choose_bz(int nz, int columns, int slots, int sms) {
 bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPlan* plan) {
   const int rbx = tile_req ? tile_req[0] : 0;
   const int rby = tile_req ? tile_req[1] : 0;
-  int rns, rwb;
-  pipeline_request(&rns, &rwb);
-  const K1Variant* v = find_variant(g.lattice, storage, rbx, rby, rns, rwb);
+  int rns, rwb, rnxw;
+  pipeline_request(&rns, &rwb, &rnxw);
+  const K1Variant* v = find_variant(g.lattice, storage, rbx, rby, rns, rwb, rnxw);
   if (!v) return false;
   FusedPlan p{};
   p.bx = v->bx;
   p.by = v->by;
   p.slots = v->ns;
   p.wbuf = v->wb;
+  p.xwarps = v->nxw;
   p.smem_bytes = v->smem;
   p.nbx = (g.nx + p.bx - 1) / p.bx;
   p.nby = (g.ny + p.by - 1) / p.by;
@@ -114,7 +118,8 @@ bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPla
 }
 
 static const K1Variant* ctx_variant(lb_ctx* ctx) {
-  return find_variant(ctx->lattice, ctx->storage, ctx->plan.bx, ctx->plan.by, ctx->plan.slots, ctx->plan.wbuf);
+  return find_variant(ctx->lattice, ctx->storage, ctx->plan.bx, ctx->plan.by, ctx->plan.slots, ctx->plan.wbuf,
+                      ctx->plan.xwarps);
 }
 
 cudaError_t k1_configure(lb_ctx* ctx) {
