@@ -41,6 +41,12 @@ WORKLOADS = {
     "tg_d3q27_512": dict(lattice="D3Q27", dims=(512, 512, 512), tau=0.8, flow="tg3d", u0=0.02),
     "tg_d3q27_256": dict(lattice="D3Q27", dims=(256, 256, 256), tau=0.8, flow="tg3d", u0=0.02),
     "tg_d2q9_16384": dict(lattice="D2Q9", dims=(16384, 16384, 1), tau=0.8, flow="tg2d", u0=0.01),
+    # force-driven channel (walls at +-y, periodic x and z) started from the
+    # analytic parabola; the force 1e-6 of an H = 64 channel is scaled by
+    # (64/512)^2 so that the peak velocity stays 0.0154 at H = 512
+    "channel_d3q27_512": dict(lattice="D3Q27", dims=(512, 512, 512), tau=0.6, flow="channel",
+                              force=1e-6 * (64.0 / 512.0) ** 2),
+    "channel_d3q27_64": dict(lattice="D3Q27", dims=(64, 64, 64), tau=0.6, flow="channel", force=1e-6),
 }
 Q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}
@@ -51,7 +57,23 @@ def boundary(w):
         faces = [1, 1, 1, 2, 1, 1]
         wall_u = [[0, 0, 0]] * 3 + [[w["lid"], 0, 0]] + [[0, 0, 0]] * 2
         return faces, wall_u
+    if w["flow"] == "channel":
+        return [0, 0, 1, 1, 0, 0], None
     return [0] * 6, None
+
+
+def force_of(w):
+    return (w.get("force", 0.0), 0.0, 0.0)
+
+
+def channel_fields(w, torch):
+    """Analytic Poiseuille profile u_x(y) = F/(2 rho0 nu) (y + 1/2)(H - 1/2 - y)
+    (walls half a link outside nodes 0 and H - 1), built on the device."""
+    nx, ny, nz = w["dims"]
+    nu = (w["tau"] - 0.5) / 3.0
+    y = torch.arange(ny, device="cuda", dtype=torch.float64)
+    prof = w["force"] / (2.0 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    return prof
 
 
 def read_peaks():
@@ -143,6 +165,16 @@ def init_state(solver, w, torch):
         solver.init_uniform(1.0, (0.0, 0.0, 0.0))
         return
     import synth
+    if w["flow"] == "channel":
+        nx, ny, nz = w["dims"]
+        N = nx * ny * nz
+        rho = torch.ones(N, device="cuda", dtype=torch.float64)
+        u = torch.zeros((3, N), device="cuda", dtype=torch.float64)
+        u[0].view(nz, ny, nx).copy_(channel_fields(w, torch).view(1, ny, 1).expand(nz, ny, nx))
+        solver.init_moments(rho, u)
+        del rho, u
+        torch.cuda.empty_cache()
+        return
     if w["flow"] == "tg3d":
         rho, u, pi = synth.taylor_green_3d_torch(w["dims"][0], w["u0"], 1.0, w["tau"], torch)
     else:
@@ -228,6 +260,7 @@ def main():
     ap.add_argument("--tile", default=None, help="bx,by,bz")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -248,7 +281,7 @@ def main():
     stream = torch.cuda.Stream()
     tile = tuple(int(v) for v in args.tile.split(",")) if args.tile else None
     s = Solver(lattice, dims, tau, faces=faces, wall_u=wall_u, storage=args.storage, scheme=args.scheme,
-               stream=stream, tile=tile)
+               stream=stream, tile=tile, force=force_of(w))
     info = s.info()
     init_state(s, w, torch)
     for _ in range(args.warmup):
@@ -299,6 +332,14 @@ def main():
         "algorithmic_bytes_per_update": 2 * q * es,
     }
 
+    # ---- accuracy: the timed run against the analytic profile (channel), and
+    # the same storage at a parity size against the FP64 path of the library
+    accuracy = {}
+    if w["flow"] == "channel":
+        accuracy["u_vs_parabola_after_timed_steps"] = channel_error(s, w, torch)
+    if not args.no_accuracy:
+        accuracy.update(side_accuracy(w, args, torch))
+
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -321,7 +362,7 @@ def main():
                        "flow": w["flow"], "l2_flush": "inputs larger than L2 (%.1f GB population array)" % (
                            info["population_bytes"] / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "accuracy": accuracy,
             "gpu_launches": launches_per_step * args.steps,
             "per_launch_ms": {"mean": float(np.mean(per_launch)), "min": float(np.min(per_launch)),
                               "max": float(np.max(per_launch))},
@@ -329,6 +370,58 @@ def main():
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def channel_error(s, w, torch):
+    """Relative L2 error of u (all nodes, all components) against the analytic
+    channel profile, in FP64 on the device."""
+    nx, ny, nz = w["dims"]
+    N = nx * ny * nz
+    rho = torch.empty(N, device="cuda", dtype=torch.float64)
+    u = torch.empty((3, N), device="cuda", dtype=torch.float64)
+    s.moments(rho, u)
+    prof = channel_fields(w, torch).view(1, ny, 1)
+    ux = u[0].view(nz, ny, nx)
+    num = ((ux - prof) ** 2).sum() + (u[1] ** 2).sum() + (u[2] ** 2).sum()
+    den = (prof.expand(nz, ny, nx) ** 2).sum()
+    out = float(torch.sqrt(num / den))
+    del rho, u
+    torch.cuda.empty_cache()
+    return out
+
+
+PARITY_SIZE = {"cavity": ((64, 64, 64), 200), "tg3d": ((64, 64, 64), 200), "tg2d": ((256, 256, 1), 1000),
+               "channel": ((64, 64, 64), 2000)}
+
+
+def side_accuracy(w, args, torch):
+    """The benchmark's storage and scheme against the library's FP64 path (the
+    path the tests hold to 1e-12 of the CPU oracle) on the same flow at a
+    parity size: relative L2 of rho and u."""
+    from paper_2304_06437_gb300 import Solver
+    dims, steps = PARITY_SIZE[w["flow"]]
+    ws = dict(w)
+    ws["dims"] = dims
+    if w["flow"] == "channel":
+        ws["force"] = 1e-6  # the H = 64 force of the channel study
+    faces, wall_u = boundary(ws)
+    out = {}
+    for storage in ("f64", args.storage):
+        s = Solver(w["lattice"], dims, w["tau"], faces=faces, wall_u=wall_u, storage=storage,
+                   scheme=args.scheme, force=force_of(ws))
+        init_state(s, ws, torch)
+        s.step(steps)
+        N = dims[0] * dims[1] * dims[2]
+        d = 2 if w["lattice"] == "D2Q9" else 3
+        rho = torch.empty(N, device="cuda", dtype=torch.float64)
+        u = torch.empty((d, N), device="cuda", dtype=torch.float64)
+        s.moments(rho, u)
+        s.close()
+        out[storage] = (rho, u)
+    (r64, u64), (r, u) = out["f64"], out[args.storage]
+    return {"vs": "library FP64 path", "size": "x".join(map(str, dims)), "steps": steps,
+            "rho_rel_l2": float(torch.linalg.norm(r - r64) / torch.linalg.norm(r64)),
+            "u_rel_l2": float(torch.linalg.norm(u - u64) / torch.linalg.norm(u64))}
 
 
 def measure_e2e(s, w, args, torch, stream):

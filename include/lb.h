@@ -27,9 +27,11 @@
  *    (incompressible He-Luo reading of section 2 with a body force F).
  *  - Pointers: arguments named *_host are host memory; with on_device != 0 a
  *    pointer is device memory of the context's device, readable/writable on
- *    the context's stream.  Caller-owned buffers are only accessed during the
- *    call; the library owns everything it allocates and frees it in
- *    lb_destroy().
+ *    the context's stream.  The library does not wait for other streams: work
+ *    that produces a device input, or still uses a device output buffer, must
+ *    be complete (or ordered before the context stream) when the call is
+ *    made.  Caller-owned buffers are only accessed during the call; the
+ *    library owns everything it allocates and frees it in lb_destroy().
  *  - Streams: work is enqueued on the context stream (lb_options.stream, or a
  *    non-blocking stream the library creates).  lb_step() returns once the
  *    work is enqueued; calls that return data synchronise the stream first.

@@ -18,13 +18,20 @@ def _is_torch_cuda(x) -> bool:
 
 
 def _ptr(x, dtype=np.float64):
-    """(pointer, on_device) of a contiguous FP64 buffer."""
+    """(pointer, on_device) of a contiguous FP64 buffer.
+
+    A torch CUDA tensor is handed over as a device pointer after the torch
+    stream that produced it has finished: the library reads and writes it on
+    its own stream, which is not ordered after torch's (without this wait the
+    library could read a tensor whose producing kernels are still running, or
+    overwrite memory that queued torch work still uses)."""
     if x is None:
         return None, 0
     if _is_torch_cuda(x):
         import torch
         if x.dtype != torch.float64 or not x.is_contiguous():
             raise ValueError("device buffers must be contiguous torch.float64 tensors")
+        torch.cuda.current_stream(x.device).synchronize()
         return ctypes.c_void_p(x.data_ptr()), 1
     if not (isinstance(x, np.ndarray) and x.dtype == dtype and x.flags["C_CONTIGUOUS"]):
         raise ValueError("host buffers must be C-contiguous float64 numpy arrays")

@@ -152,23 +152,33 @@ def uniform_noise(shape, seed: int = SEED) -> np.ndarray:
 # ------------------------------------------------------------------ on device
 # The same analytic fields generated with torch on the GPU, for grids too large
 # to build on the host (e.g. 512^3).  Same formulas as the numpy versions.
-def taylor_green_3d_torch(n: int, u0: float, rho0: float, tau: float, torch, device="cuda"):
+def taylor_green_3d_torch(n: int, u0: float, rho0: float, tau: float, torch, device="cuda", pineq=True):
+    """taylor_green_3d on the device.  Every field is an outer product of 1D
+    sine / cosine vectors, so each output is allocated once (1024^3 fits)."""
     k = 2.0 * math.pi / n
-    ar = torch.arange(n, device=device, dtype=torch.float64)
-    z, y, x = torch.meshgrid(ar, ar, ar, indexing="ij")
-    sx, cx = torch.sin(k * x), torch.cos(k * x)
-    sy, cy = torch.sin(k * y), torch.cos(k * y)
-    sz, cz = torch.sin(k * z), torch.cos(k * z)
-    u = torch.stack([u0 * sx * cy * cz, -u0 * cx * sy * cz, torch.zeros_like(x)]).reshape(3, -1)
-    p = rho0 * u0 * u0 / 16.0 * (torch.cos(2 * k * x) + torch.cos(2 * k * y)) * (torch.cos(2 * k * z) + 2.0)
-    rho = (rho0 + p / CS2).reshape(-1)
+    ar = torch.arange(n, device=device, dtype=torch.float64) * k
+    s1, c1 = torch.sin(ar), torch.cos(ar)
+    sx, cx = s1.view(1, 1, n), c1.view(1, 1, n)
+    sy, cy = s1.view(1, n, 1), c1.view(1, n, 1)
+    sz, cz = s1.view(n, 1, 1), c1.view(n, 1, 1)
+    N = n * n * n
+    u = torch.empty((3, N), device=device, dtype=torch.float64)
+    u[0].view(n, n, n).copy_((u0 * sx * cy) * cz)
+    u[1].view(n, n, n).copy_((-u0 * cx * sy) * cz)
+    u[2].zero_()
+    c2 = torch.cos(2.0 * ar)
+    rho = ((c2.view(1, 1, n) + c2.view(1, n, 1)) * (rho0 * u0 * u0 / 16.0 / CS2)) * (c2.view(n, 1, 1) + 2.0)
+    rho = (rho + rho0).reshape(N)
+    if not pineq:
+        return rho.contiguous(), u, None
     s = -rho0 * CS2 * tau
-    pineq = torch.stack([
-        s * 2 * (u0 * k * cx * cy * cz), s * 2 * (-u0 * k * cx * cy * cz), torch.zeros_like(x),
-        s * ((-u0 * k * sx * sy * cz) + (u0 * k * sx * sy * cz)), s * (-u0 * k * sx * cy * sz),
-        s * (u0 * k * cx * sy * sz),
-    ]).reshape(6, -1)
-    return rho.contiguous(), u.contiguous(), pineq.contiguous()
+    pi = torch.zeros((6, N), device=device, dtype=torch.float64)
+    # d_x u = u0 k cx cy cz, d_y v = -u0 k cx cy cz; d_y u + d_x v = 0
+    pi[0].view(n, n, n).copy_((s * 2 * u0 * k * cx * cy) * cz)
+    pi[1].copy_(-pi[0])
+    pi[4].view(n, n, n).copy_((s * (-u0 * k) * sx * cy) * sz)  # d_z u
+    pi[5].view(n, n, n).copy_((s * u0 * k * cx * sy) * sz)  # d_z v
+    return rho.contiguous(), u, pi
 
 
 def taylor_green_2d_torch(n: int, u0: float, rho0: float, tau: float, torch, device="cuda"):
