@@ -47,6 +47,10 @@ WORKLOADS = {
     "channel_d3q27_512": dict(lattice="D3Q27", dims=(512, 512, 512), tau=0.6, flow="channel",
                               force=1e-6 * (64.0 / 512.0) ** 2),
     "channel_d3q27_64": dict(lattice="D3Q27", dims=(64, 64, 64), tau=0.6, flow="channel", force=1e-6),
+    # 256 independent domains in one batch: 128 D2Q9 squares (side log-uniform
+    # 32..1024) and 128 D3Q19 cubes (16..128), tau uniform in [0.55, 1.2], per
+    # lattice half Taylor-Green (periodic) and half lid-driven cavity, FP32
+    "batch_256": dict(lattice="mixed", dims=None, tau=None, flow="batch", n2d=128, n3d=128),
 }
 Q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}
@@ -266,6 +270,9 @@ def main():
     if args.impl == "reference":
         run_reference(args, w)
         return
+    if w["flow"] == "batch":
+        run_batch(args, w)
+        return
 
     import torch
     ws, rank, local = dist_env()
@@ -366,6 +373,130 @@ def main():
             "gpu_launches": launches_per_step * args.steps,
             "per_launch_ms": {"mean": float(np.mean(per_launch)), "min": float(np.min(per_launch)),
                               "max": float(np.max(per_launch))},
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def batch_specs(w, seed=20230412):
+    """Domain list of the batching workload (seeded)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for lat, n, lo, hi, u0 in (("D2Q9", w["n2d"], 32, 1024, 0.01), ("D3Q19", w["n3d"], 16, 128, 0.02)):
+        for i in range(n):
+            L = int(round(math.exp(g.uniform(math.log(lo), math.log(hi)))))
+            tau = float(g.uniform(0.55, 1.2))
+            flow = "tg" if i < n // 2 else "cavity"
+            out.append(dict(lattice=lat, L=L, tau=tau, flow=flow, u0=u0))
+    return out
+
+
+def make_batch_domain(spec, storage, torch, stream=None):
+    from paper_2304_06437_gb300 import Solver
+    import synth
+    lat, L, tau = spec["lattice"], spec["L"], spec["tau"]
+    d = 2 if lat == "D2Q9" else 3
+    dims = (L, L) if d == 2 else (L, L, L)
+    if spec["flow"] == "cavity":
+        faces = [1, 1, 1, 2, 1, 1] if d == 3 else [1, 1, 1, 2, 0, 0]
+        wall_u = [[0, 0, 0]] * 3 + [[0.05, 0, 0]] + [[0, 0, 0]] * 2
+        s = Solver(lat, dims, tau, faces=faces, wall_u=wall_u, storage=storage, stream=stream)
+        s.init_uniform(1.0)
+        return s
+    s = Solver(lat, dims, tau, storage=storage, stream=stream)
+    if d == 3:
+        rho, u, pi = synth.taylor_green_3d_torch(L, spec["u0"], 1.0, tau, torch)
+    else:
+        rho, u, pi = synth.taylor_green_2d_torch(L, spec["u0"], 1.0, tau, torch)
+    s.init_moments(rho, u, pi)
+    return s
+
+
+def run_batch(args, w):
+    """Batching workload: all domains advance together, one persistent launch
+    per brick-shape class and step, two steps per CUDA-graph replay; compared
+    with the same domains stepped one after another with the single-domain
+    kernel (one launch per domain and step)."""
+    import torch
+    from paper_2304_06437_gb300 import Batch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    specs = batch_specs(w)
+    stream = torch.cuda.Stream()
+    doms = [make_batch_domain(sp, args.storage, torch, stream) for sp in specs]
+    torch.cuda.synchronize()
+    N = sum(d.n for d in doms)
+    q_of = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}
+    es = STORAGE_BYTES[args.storage]
+    alg_bytes = sum(2 * q_of[sp["lattice"]] * es * d.n for sp, d in zip(specs, doms))
+    b = Batch(doms, stream=stream)
+    info = b.info()
+    b.step(args.warmup)
+    b.sync()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    b.sync()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    total_ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * N * args.steps / (total_ms * 1e-3) / 1e6
+    # the same domains one after another, one single-domain launch each
+    seq_steps = max(2, min(args.steps, 20))
+    for d in doms:
+        d.step(1)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(seq_steps):
+        for d in doms:
+            d.step(1)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = s0.elapsed_time(s1) / seq_steps
+    seq_value = N / (seq_ms * 1e-3) / 1e6
+    b.close()
+    for d in doms:
+        d.close()
+    peak, peak_kind = read_peaks()
+    achieved = alg_bytes / (total_ms / args.steps * 1e-3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "domains": len(specs), "nodes": N, "storage": args.storage,
+                       "classes": info["n_classes"], "persistent_ctas": info["ctas"],
+                       "work_items": info["work_items"], "graph": "2 steps per replay",
+                       "l2_flush": "none: %.1f GB of populations per step, larger than L2" % (alg_bytes / 2e9),
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "traffic": None, "kernel": "k2_batched_step (all classes)",
+                         "algorithmic_bytes_per_step": alg_bytes},
+            "sequential_baseline": {"value": seq_value, "unit": "MLUPS", "ms_per_step": seq_ms,
+                                    "what": "same domains, one single-domain launch per domain and step"},
+            "cpu_baseline": None, "e2e": None, "clocks": clk,
+            "gpu_launches": info["launches_per_step"] * args.steps,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

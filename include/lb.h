@@ -109,6 +109,8 @@ typedef struct {
   uint64_t population_bytes; /* the one population array */
   uint64_t aux_bytes;        /* shells (fused) or moment arrays (two-pass) */
   uint64_t algorithmic_bytes_per_update; /* 2 q s: one read + one write per population */
+  int32_t nodes_per_thread;  /* fused scheme: 1 scalar kernel, 2 paired FP32x2 kernel */
+  int32_t tma_slots;         /* fused scheme: TMA ring depth */
 } lb_info_t;
 
 /* Fills *opt with the defaults listed above. */
@@ -208,6 +210,75 @@ LB_API int lb_memory_plan(int32_t lattice, int32_t bytes_per_value, lb_memory_pl
 #define LB_NOALLOC_SCRATCH_BYTES (64ull << 20)
 LB_API int lb_step_noalloc(int32_t lattice, const int64_t dims[3], double tau, const lb_boundary* bnd,
                            double rho0, const double force[3], double* f, int64_t n, void* stream);
+
+/* ---------------------------------------------------------------- autotuner
+ * Picks the fused step's brick shape for a context by measurement (the paper
+ * tunes nothing; its thread blocks are fixed, elongated along x).  Every
+ * compiled shape of the context's lattice and storage -- brick bx x by, TMA
+ * pipeline depth, one or two nodes per thread -- is timed for `steps` steps
+ * on a proxy domain with the same cross-section, boundaries, tau and force and
+ * at most ~4 GB of populations (the sweep axis shortened; the proxy is
+ * allocated and freed inside the call, on the context's device).  The fastest
+ * per node update is applied to the context: new shell buffers and TMA
+ * descriptor, the shell rebuilt from the current populations, which are not
+ * changed (every shape computes the same bits).  The choice is cached per
+ * (lattice, storage, cross-section, sweep length rounded up to a power of two,
+ * face kinds, forcing); a cached kind is applied without timing and reports
+ * *n_entries = 0.  table (may be NULL) receives up to cap entries, one per
+ * shape timed.  Synchronises the context stream.  Errors: LB_E_INVAL,
+ * LB_E_UNSUPPORTED (two-pass scheme), LB_E_NOMEM, LB_E_CUDA. */
+typedef struct {
+  int32_t bx, by, bz;          /* brick and the sweep length the planner gave the proxy */
+  int32_t slots;               /* TMA ring depth */
+  int32_t nodes_per_thread;    /* 1 scalar, 2 paired FP32x2 kernel */
+  int32_t export_warps;        /* dedicated shell-export warps (0: shared) */
+  int32_t status;              /* LB_OK, or why this shape could not be timed */
+  double ns_per_update;        /* measured time per node update; -1 if not timed */
+} lb_tune_entry;
+LB_API int lb_autotune(lb_ctx* ctx, int32_t steps, lb_tune_entry* table, int32_t cap, int32_t* n_entries);
+
+/* ------------------------------------------------------------------ batches
+ * Many independent domains stepped together (the paper steps one domain; a
+ * batch serves many small ones, which alone cannot fill the GPU).
+ *
+ * lb_batch_create groups n existing contexts of the fused scheme on one device
+ * (any lattices, sizes, tau, boundaries and forces).  Contexts that share a
+ * compiled brick shape and the forcing switch form a class; per time step each
+ * class runs ONE persistent launch whose CTAs sweep a static, cost-balanced
+ * list of the brick columns of all its domains, and the launches of two
+ * consecutive steps are captured once in a CUDA graph and replayed.  The
+ * populations of every domain are bit for bit those of stepping it alone.
+ * Every storage is batched; two-pass contexts give LB_E_UNSUPPORTED.  The
+ * batch keeps
+ * pointers to the contexts, which must outlive it and must not be re-planned
+ * while it exists; stepping a member alone between batch steps is allowed.
+ * stream: cudaStream_t for the batch's work, NULL = a library-owned stream.
+ * Errors: LB_E_INVAL (NULL, duplicates, mixed devices), LB_E_UNSUPPORTED,
+ * LB_E_NOMEM, LB_E_CUDA. */
+typedef struct lb_batch lb_batch;
+typedef struct {
+  int32_t n_domains, n_classes;
+  int32_t launches_per_step;  /* one per class */
+  int32_t ctas;               /* persistent CTAs over all classes */
+  int64_t work_items;         /* brick columns over all domains */
+  int64_t total_nodes;
+  int64_t steps_done;
+} lb_batch_info_t;
+LB_API int lb_batch_create(lb_ctx* const* ctxs, int32_t n, void* stream, lb_batch** out);
+
+/* Enqueues n time steps of every member (asynchronous).  The batch stream
+ * first waits for work already queued on the members' own streams, and
+ * afterwards each member's stream waits for the batch, so lb_moments() and
+ * friends on a member see the batch's steps. */
+LB_API int lb_batch_step(lb_batch* b, int64_t n);
+
+/* Waits for the batch stream; returns LB_E_TIMEOUT if a kernel of the batch
+ * gave up waiting for a copy. */
+LB_API int lb_batch_sync(lb_batch* b);
+LB_API int lb_batch_info(const lb_batch* b, lb_batch_info_t* info);
+
+/* Frees the batch (not its contexts).  NULL is allowed. */
+LB_API void lb_batch_destroy(lb_batch* b);
 
 /* Human-readable name of a status code. */
 LB_API const char* lb_status_string(int code);

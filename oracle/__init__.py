@@ -12,6 +12,10 @@ Two implementations live here:
 * ``brute.py`` -- an independent numpy brute force for tiny grids that reaches
   the regularized set by a numerical weighted least-squares projection instead
   of the closed form, used to cross-check the C oracle.
+* ``storage.py`` -- round-to-nearest-even of the shifted populations to the
+  reduced storage formats (FP16, BF16), from the formats' definitions; with
+  ``run_stored`` below it gives the exact reference of a reduced-precision run
+  (FP64 arithmetic, rounded storage after every step).
 
 The Python wrapper below only marshals numpy arrays into the C entry points.
 """
@@ -193,6 +197,17 @@ def moments(cfg: OrcCfg, f: np.ndarray):
     if rc != 0:
         raise ValueError("orc_moments rejected the configuration (rc=%d)" % rc)
     return rho, u
+
+
+def run_stored(cfg: OrcCfg, f: np.ndarray, steps: int, storage: str, threads: int = 0) -> np.ndarray:
+    """Advance f by `steps`, rounding the stored (shifted) populations to the
+    storage format after every step; f itself should already be stored values."""
+    from .storage import round_populations
+    w = lattice_tables(cfg.lattice)[1]
+    out = np.ascontiguousarray(f, dtype=np.float64).copy()
+    for _ in range(int(steps)):
+        out = round_populations(run(cfg, out, 1, threads), w, storage, cfg.rho0)
+    return out
 
 
 def max_threads() -> int:

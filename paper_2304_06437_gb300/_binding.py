@@ -61,6 +61,8 @@ class lb_info_t(ctypes.Structure):
         ("population_bytes", ctypes.c_uint64),
         ("aux_bytes", ctypes.c_uint64),
         ("algorithmic_bytes_per_update", ctypes.c_uint64),
+        ("nodes_per_thread", ctypes.c_int32),
+        ("tma_slots", ctypes.c_int32),
     ]
 
 
@@ -74,6 +76,31 @@ class lb_memory_plan_t(ctypes.Structure):
         ("bytes_per_node_moment_scheme", ctypes.c_double),
         ("bytes_per_node_flip_flop", ctypes.c_double),
         ("bytes_per_node_single", ctypes.c_double),
+    ]
+
+
+class lb_tune_entry(ctypes.Structure):
+    _fields_ = [
+        ("bx", ctypes.c_int32),
+        ("by", ctypes.c_int32),
+        ("bz", ctypes.c_int32),
+        ("slots", ctypes.c_int32),
+        ("nodes_per_thread", ctypes.c_int32),
+        ("export_warps", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+        ("ns_per_update", ctypes.c_double),
+    ]
+
+
+class lb_batch_info_t(ctypes.Structure):
+    _fields_ = [
+        ("n_domains", ctypes.c_int32),
+        ("n_classes", ctypes.c_int32),
+        ("launches_per_step", ctypes.c_int32),
+        ("ctas", ctypes.c_int32),
+        ("work_items", ctypes.c_int64),
+        ("total_nodes", ctypes.c_int64),
+        ("steps_done", ctypes.c_int64),
     ]
 
 
@@ -107,6 +134,12 @@ SIGNATURES = {
     "lb_memory_plan": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P(lb_memory_plan_t)]),
     "lb_step_noalloc": (ctypes.c_int, [ctypes.c_int32, _i64p, ctypes.c_double, _P(lb_boundary), ctypes.c_double,
                                        _dp, _vp, ctypes.c_int64, _vp]),
+    "lb_autotune": (ctypes.c_int, [_vp, ctypes.c_int32, _P(lb_tune_entry), ctypes.c_int32, _P(ctypes.c_int32)]),
+    "lb_batch_create": (ctypes.c_int, [_P(_vp), ctypes.c_int32, _vp, _P(_vp)]),
+    "lb_batch_step": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "lb_batch_sync": (ctypes.c_int, [_vp]),
+    "lb_batch_info": (ctypes.c_int, [_vp, _P(lb_batch_info_t)]),
+    "lb_batch_destroy": (None, [_vp]),
     "lb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lb_abi_version": (ctypes.c_int, []),
 }

@@ -129,6 +129,46 @@ struct DeviceGuard {
 
 }  // namespace
 
+namespace lbgb {
+
+int ctx_replan(lb_ctx* ctx, const void* variant) {
+  if (!ctx || ctx->scheme != LB_SCHEME_FUSED) return LB_E_INVAL;
+  FusedPlan p;
+  if (!k1_plan_variant(ctx->g, variant, &p)) return LB_E_INVAL;
+  DeviceGuard guard(ctx->device);
+  LB_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+  const size_t aux_bytes = size_t(2) * size_t(p.parity_elems) * ctx->real_bytes;
+  void* aux = nullptr;
+  LB_TRY_CUDA(cudaMalloc(&aux, aux_bytes));
+  cudaError_t e = cudaMemsetAsync(aux, 0, aux_bytes, ctx->stream);
+  if (e != cudaSuccess) {
+    cudaFree(aux);
+    return cuda_status(e);
+  }
+  const FusedPlan old_plan = ctx->plan;
+  void* old_aux = ctx->aux;
+  const size_t old_bytes = ctx->aux_bytes;
+  ctx->plan = p;
+  ctx->aux = aux;
+  ctx->aux_bytes = aux_bytes;
+  int rc = make_tensor_map(ctx);
+  if (rc == LB_OK) rc = cuda_status(k1_configure(ctx));
+  if (rc == LB_OK) rc = after_state_change(ctx);  // rebuild the shell from the populations
+  if (rc == LB_OK) rc = cuda_status(cudaStreamSynchronize(ctx->stream));
+  if (rc != LB_OK) {
+    ctx->plan = old_plan;
+    ctx->aux = old_aux;
+    ctx->aux_bytes = old_bytes;
+    make_tensor_map(ctx);
+    cudaFree(aux);
+    return rc;
+  }
+  cudaFree(old_aux);
+  return LB_OK;
+}
+
+}  // namespace lbgb
+
 extern "C" {
 
 int lb_abi_version(void) { return LB_ABI_VERSION; }
@@ -228,6 +268,9 @@ int lb_create(int32_t lattice, const int64_t dims[3], double tau, const lb_bound
 
   lb_ctx* ctx = new (std::nothrow) lb_ctx();
   if (!ctx) return LB_E_NOMEM;
+  ctx->bnd_user = b;
+  ctx->opt_user = opt;
+  ctx->tau_user = tau;
   ctx->lattice = lattice;
   ctx->storage = opt.storage;
   ctx->scheme = opt.scheme;
@@ -518,6 +561,8 @@ int lb_info(const lb_ctx* ctx, lb_info_t* info) {
     info->tile[0] = ctx->plan.bx;
     info->tile[1] = ctx->plan.by;
     info->tile[2] = ctx->plan.bz;
+    info->nodes_per_thread = ctx->plan.npt;
+    info->tma_slots = ctx->plan.slots;
   }
   info->population_bytes = ctx->f_bytes;
   info->aux_bytes = ctx->aux_bytes;

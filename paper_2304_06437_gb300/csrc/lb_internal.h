@@ -36,6 +36,7 @@ struct FusedPlan {
   int slots;               // TMA pipeline depth
   int wbuf;                // shared window buffers (2: one barrier per plane)
   int xwarps;              // dedicated export warps (0: node-owning warps export)
+  int npt;                 // nodes per thread (1 scalar, 2 paired FP32x2 kernel)
   size_t smem_bytes;
 };
 
@@ -45,6 +46,9 @@ struct Status;
 
 struct lb_ctx {
   lbgb::Geometry g;
+  lb_boundary bnd_user;   // the creation arguments as given (for proxies of the autotuner)
+  lb_options opt_user;
+  double tau_user;
   int32_t lattice, storage, scheme;
   int64_t dims[3];
   int64_t n_nodes;
@@ -76,6 +80,13 @@ cudaError_t k0_step_buffers(const Geometry& g, double* ft, double* mom, cudaStre
 
 // ---- fused scheme (lb_k1_*.cu)
 bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPlan* plan);
+// plan with one given compiled shape (a K1Variant*, see lb_k1_launch.cuh)
+bool k1_plan_variant(const Geometry& g, const void* variant, FusedPlan* plan);
+// compiled shapes for (lattice, storage), in the planner's order; returns the count
+int k1_variants_for(int lattice, int storage, const void** out, int cap);
+// switch a fused-scheme context to another compiled shape: new shell buffers
+// and TMA descriptor, shell rebuilt from the current populations (lb_capi.cu)
+int ctx_replan(lb_ctx* ctx, const void* variant);
 cudaError_t k1_step(lb_ctx* ctx);
 cudaError_t k1_bootstrap(lb_ctx* ctx);  // fill the current shell parity from f
 cudaError_t k1_configure(lb_ctx* ctx);  // one-time kernel attributes

@@ -258,9 +258,14 @@ __device__ __forceinline__ void export_lateral(const K1Args<R>& args, const R (&
   }
 }
 
+// The sweep of one brick column (bI, bJ, bK) of one domain by the whole CTA.
+// tmap_p is the domain's TMA descriptor (kernel-parameter or global memory).
+// Returns false if a TMA wait timed out (the CTA recorded LB_E_TIMEOUT and
+// must stop).  On return every copy the brick issued has completed and the
+// mbarriers are invalidated, so the CTA may start another brick.
 template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE>
-__global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
-    k1_fused_step(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ K1Args<R> args) {
+__device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args<R>& args, const int bI,
+                                         const int bJ, const int bK) {
   using Sh = K1Shape<L, S, R, BX, BY, NS, WB, NXW>;
   static_assert(WB == 2, "the pipelined sweep needs two window buffers");
   constexpr int Q = L::Q;
@@ -290,9 +295,6 @@ __global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
   const int warp = tid / 32, lane = tid % 32;
   const int nx = args.nx, ny = args.ny, nz = args.nz;
   const int nbx = args.nbx, nby = args.nby, nbz = args.nbz;
-  const int bI = blockIdx.x % nbx;
-  const int bJ = (blockIdx.x / nbx) % nby;
-  const int bK = blockIdx.x / (nbx * nby);
   const int x0 = bI * BX, y0 = bJ * BY, z0 = bK * args.bz;
   const int bxa = min(BX, nx - x0), bya = min(BY, ny - y0);
   const int z1 = min(z0 + args.bz, nz);
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
     fence_barrier_init();
-    prefetch_tmap(&tmap);
+    prefetch_tmap(tmap_p);
   }
   __syncthreads();
   int issued = 0;  // real planes whose load was issued (thread 0's view)
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
       const int zz = z0 + s;
       if (zz < z1) {
         mbar_arrive_expect_tx(&bars[s], static_cast<uint32_t>(Sh::SLOT));
-        tma_load_4d(slots + size_t(s) * Q * BY * BX, &tmap, x0, y0, zz, 0, &bars[s]);
+        tma_load_4d(slots + size_t(s) * Q * BY * BX, tmap_p, x0, y0, zz, 0, &bars[s]);
         ++issued;
       }
     }
@@ -510,15 +512,17 @@ __global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
         }
       });
     }
-    if (plane_needed(c)) {
-      // only valid entries: an invalid north/south entry of a ragged brick
-      // would alias the east ring's corner cell of a diagonal direction
-#pragma unroll
-      for (int e = 0; e < HPT; ++e)
-        if (hval[e]) win[hsm[e]] = ha[e];
-    }
     return true;
   };
+  // the ring of the window of plane c (values fetched two planes ahead); kept
+  // out of the lambda above so the ring arrays stay in registers.  Only valid
+  // entries: an invalid north/south entry of a ragged brick would alias the
+  // east ring's corner cell of a diagonal direction.
+#define LB_RING_PUT(win_, c_)                          \
+  if (plane_needed(c_)) {                              \
+    _Pragma("unroll") for (int e = 0; e < HPT; ++e)    \
+      if (hval[e]) (win_)[hsm[e]] = ha[e];             \
+  }
 
   // three destination planes of gathered populations
   R G0[Q], G1[Q], G2[Q];  // planes g-1, g, g+1 of the plane g being gathered
@@ -548,9 +552,10 @@ __global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
   R onl_g[3] = {R(0), R(0), R(0)};  // non-lateral populations of the gathered plane
   {
     bool ok = produce(z0 - 1, win0 + ((z0 - 1) & 1) * WSTRIDE, onl_g);
+    if (is_main) LB_RING_PUT(win0 + ((z0 - 1) & 1) * WSTRIDE, z0 - 1);
     if (__syncthreads_or(!ok)) {
       abort_cta(0);
-      return;
+      return false;
     }
   }
 #pragma unroll
@@ -568,7 +573,10 @@ __global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
 
     R onl_c[3] = {R(0), R(0), R(0)};
     bool ok = true;
-    if (c <= z1) ok = produce(c, win_c, onl_c);
+    if (c <= z1) {
+      ok = produce(c, win_c, onl_c);
+      if (is_main) LB_RING_PUT(win_c, c);
+    }
 
     // gather plane g (window complete since the previous barrier)
     if (active && need_g) {
@@ -669,19 +677,56 @@ __global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
     // every thread has left plane g's buffers, which plane c + 1 reuses
     if (__syncthreads_or(!ok)) {
       abort_cta(c - z0);
-      return;
+      return false;
     }
     // refill the slot consumed by plane c with plane c + NS
     if (tid == 0 && c >= z0 && c < z1 && c + NS < z1) {
       const int slot = (c - z0) % NS;
       mbar_arrive_expect_tx(&bars[slot], static_cast<uint32_t>(Sh::SLOT));
-      tma_load_4d(slots + size_t(slot) * Q * BY * BX, &tmap, x0, y0, c + NS, 0, &bars[slot]);
+      tma_load_4d(slots + size_t(slot) * Q * BY * BX, tmap_p, x0, y0, c + NS, 0, &bars[slot]);
       ++issued;
     }
   }
 
   // exports of the last two planes
   export_staged(z1 - 1);
+  // every issued plane has been waited for: retire the barriers so that the
+  // next brick of a persistent CTA can initialise them again
+  __syncthreads();
+  if (tid == 0)
+    for (int s = 0; s < NS; ++s) mbar_inval(&bars[s]);
+  __syncthreads();
+  return true;
+#undef LB_RING_PUT
+}
+
+// One launch per time step of one domain: one CTA per brick column.
+template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE>
+__global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
+    k1_fused_step(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ K1Args<R> args) {
+  const int nbx = args.nbx, nby = args.nby;
+  const int b = blockIdx.x;
+  k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE>(&tmap, args, b % nbx, (b / nbx) % nby, b / (nbx * nby));
+}
+
+// One launch per time step of many domains (a batch): a persistent grid whose
+// CTA i sweeps the bricks items[starts[i] .. starts[i+1]) in turn.  An item is
+// (domain, bI, bJ, bK); the arguments of domain d at shell parity p are
+// args[p * n_dom + d], and domain d's parity at this launch is
+// (dom_par[d] + k) & 1.
+template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE>
+__global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
+    k1_batched_step(const K1Args<R>* __restrict__ args, int n_dom, const CUtensorMap* __restrict__ tmaps,
+                    const int4* __restrict__ items, const int* __restrict__ starts, const int* __restrict__ dom_par,
+                    int k) {
+  const int i1 = starts[blockIdx.x + 1];
+  for (int i = starts[blockIdx.x]; i < i1; ++i) {
+    const int4 it = items[i];
+    const int p = (dom_par[it.x] + k) & 1;
+    if (!k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE>(tmaps + it.x, args[size_t(p) * n_dom + it.x], it.y, it.z,
+                                                       it.w))
+      return;
+  }
 }
 
 // Shell bootstrap: collide every brick-boundary node of the current state and

@@ -6,13 +6,37 @@
 
 namespace lbgb {
 
+// Device-side description of one batched launch (see lb_batch.cu): the
+// per-domain arguments at both shell parities, TMA descriptors, the static
+// work list of brick items and each CTA's slice of it.
+struct BatchLaunch {
+  const void* args;  // K1Args<R>[2][n_dom], R the arithmetic type of the variant
+  int n_dom;
+  const CUtensorMap* tmaps;
+  const int4* items;
+  const int* starts;
+  const int* dom_par;
+  int grid;
+  int k;      // step within the captured pair (0 or 1)
+  bool force;
+};
+
 struct K1Variant {
   int lattice, storage, bx, by, ns, wb, nxw;
   size_t smem;
   cudaError_t (*configure)();
   cudaError_t (*step)(lb_ctx*);
   cudaError_t (*bootstrap)(lb_ctx*);
+  int npt;  // nodes per thread: 1 = scalar kernel (lb_k1.cuh), 2 = paired kernel (lb_k2.cuh)
+  // batched persistent launch (paired kernels only; null otherwise) and the
+  // number of its CTAs that fit on one SM
+  cudaError_t (*batched)(const BatchLaunch&, cudaStream_t);
+  int (*batched_occupancy)();
 };
+
+// the compiled shape a fused-scheme context runs (lb_k1_plan.cu)
+const K1Variant* k1_ctx_variant(lb_ctx* ctx);
+int k1_sm_count();
 
 template <class R>
 K1Args<R> k1_make_args(lb_ctx* ctx, int cur_parity, int next_parity) {
@@ -79,8 +103,35 @@ struct K1Impl {
     return cudaGetLastError();
   }
 
+  static cudaError_t batched(const BatchLaunch& b, cudaStream_t stream) {
+    const K1Args<R>* args = static_cast<const K1Args<R>*>(b.args);
+    if (b.force)
+      k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true><<<b.grid, Sh::NT, Sh::SMEM, stream>>>(
+          args, b.n_dom, b.tmaps, b.items, b.starts, b.dom_par, b.k);
+    else
+      k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, false><<<b.grid, Sh::NT, Sh::SMEM, stream>>>(
+          args, b.n_dom, b.tmaps, b.items, b.starts, b.dom_par, b.k);
+    return cudaGetLastError();
+  }
+
+  static int batched_occupancy() {
+    const int sm = int(Sh::SMEM);
+    if (configure() != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
+      return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true>, Sh::NT,
+                                                      Sh::SMEM) != cudaSuccess)
+      return 0;
+    return n;
+  }
+
   static constexpr K1Variant variant(int lattice, int storage) {
-    return K1Variant{lattice, storage, BX, BY, NS, WB, NXW, Sh::SMEM, &configure, &step, &bootstrap};
+    return K1Variant{lattice, storage, BX, BY, NS, WB, NXW, Sh::SMEM, &configure, &step, &bootstrap, 1, &batched,
+                     &batched_occupancy};
   }
 };
 

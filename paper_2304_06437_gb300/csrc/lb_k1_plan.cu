@@ -13,40 +13,67 @@ extern const K1Variant k1_variants_d3q19[];
 extern const int k1_n_variants_d3q19;
 extern const K1Variant k1_variants_d3q27[];
 extern const int k1_n_variants_d3q27;
+extern const K1Variant k2_variants_d2q9[];
+extern const int k2_n_variants_d2q9;
+extern const K1Variant k2_variants_d3q19[];
+extern const int k2_n_variants_d3q19;
+extern const K1Variant k2_variants_d3q27[];
+extern const int k2_n_variants_d3q27;
+
+// The compiled brick shapes of a lattice in the planner's order of
+// preference: for D2Q9 the paired kernels (two nodes per thread, FP32x2) come
+// first, for D3Q19 / D3Q27 the scalar ones, which measure faster there (the
+// paired 3D kernels need ~230 registers per thread and run 8 warps per SM).
+static int variant_lists(int lattice, const K1Variant* lists[2], int counts[2]) {
+  switch (lattice) {
+    case LB_D2Q9:
+      lists[0] = k2_variants_d2q9; counts[0] = k2_n_variants_d2q9;
+      lists[1] = k1_variants_d2q9; counts[1] = k1_n_variants_d2q9;
+      return 2;
+    case LB_D3Q19:
+      lists[0] = k1_variants_d3q19; counts[0] = k1_n_variants_d3q19;
+      lists[1] = k2_variants_d3q19; counts[1] = k2_n_variants_d3q19;
+      return 2;
+    case LB_D3Q27:
+      lists[0] = k1_variants_d3q27; counts[0] = k1_n_variants_d3q27;
+      lists[1] = k2_variants_d3q27; counts[1] = k2_n_variants_d3q27;
+      return 2;
+    default: return 0;
+  }
+}
 
 // The first compiled shape that matches (lattice, storage, bx, by, ns, wb,
-// nxw); zero fields (negative nxw) match anything.
-static const K1Variant* find_variant(int lattice, int storage, int bx, int by, int ns, int wb, int nxw) {
-  const K1Variant* list = nullptr;
-  int n = 0;
-  switch (lattice) {
-    case LB_D2Q9: list = k1_variants_d2q9; n = k1_n_variants_d2q9; break;
-    case LB_D3Q19: list = k1_variants_d3q19; n = k1_n_variants_d3q19; break;
-    case LB_D3Q27: list = k1_variants_d3q27; n = k1_n_variants_d3q27; break;
-    default: return nullptr;
-  }
-  for (int i = 0; i < n; ++i) {
-    const K1Variant& v = list[i];
-    if (v.storage != storage) continue;
-    if (bx > 0 && v.bx != bx) continue;
-    if (by > 0 && v.by != by) continue;
-    if (ns > 0 && v.ns != ns) continue;
-    if (wb > 0 && v.wb != wb) continue;
-    if (nxw >= 0 && v.nxw != nxw) continue;
-    return &v;
+// nxw, npt); zero fields (negative nxw) match anything.
+static const K1Variant* find_variant(int lattice, int storage, int bx, int by, int ns, int wb, int nxw, int npt) {
+  const K1Variant* lists[2];
+  int counts[2];
+  const int nl = variant_lists(lattice, lists, counts);
+  for (int l = 0; l < nl; ++l) {
+    for (int i = 0; i < counts[l]; ++i) {
+      const K1Variant& v = lists[l][i];
+      if (v.storage != storage) continue;
+      if (bx > 0 && v.bx != bx) continue;
+      if (by > 0 && v.by != by) continue;
+      if (ns > 0 && v.ns != ns) continue;
+      if (wb > 0 && v.wb != wb) continue;
+      if (nxw >= 0 && v.nxw != nxw) continue;
+      if (npt > 0 && v.npt != npt) continue;
+      return &v;
+    }
   }
   return nullptr;
 }
 
-// Optional pipeline request from the environment, "NS,WB[,NXW]" (TMA slots,
-// window buffers, dedicated export warps), used to compare the compiled
-// alternatives of a brick shape.
-static void pipeline_request(int* ns, int* wb, int* nxw) {
+// Optional pipeline request from the environment, "NS,WB[,NXW[,NPT]]" (TMA
+// slots, window buffers, dedicated export warps, nodes per thread), used to
+// compare the compiled alternatives of a brick shape; 0 (-1 for NXW) = any.
+static void pipeline_request(int* ns, int* wb, int* nxw, int* npt) {
   *ns = 0;
   *wb = 0;
   *nxw = -1;
+  *npt = 0;
   const char* e = std::getenv("LB_FUSED_PIPELINE");
-  if (e) std::sscanf(e, "%d,%d,%d", ns, wb, nxw);
+  if (e) std::sscanf(e, "%d,%d,%d,%d", ns, wb, nxw, npt);
 }
 
 static int sm_count() {
@@ -79,24 +106,18 @@ static int choose_bz(int nz, int columns, int slots, int sms) {
   return best_bz;
 }
 
-bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPlan* plan) {
-  const int rbx = tile_req ? tile_req[0] : 0;
-  const int rby = tile_req ? tile_req[1] : 0;
-  int rns, rwb, rnxw;
-  pipeline_request(&rns, &rwb, &rnxw);
-  const K1Variant* v = find_variant(g.lattice, storage, rbx, rby, rns, rwb, rnxw);
-  if (!v) return false;
+static void fill_plan(const Geometry& g, const K1Variant* v, int req_bz, FusedPlan* plan) {
   FusedPlan p{};
   p.bx = v->bx;
   p.by = v->by;
   p.slots = v->ns;
   p.wbuf = v->wb;
   p.xwarps = v->nxw;
+  p.npt = v->npt;
   p.smem_bytes = v->smem;
   p.nbx = (g.nx + p.bx - 1) / p.bx;
   p.nby = (g.ny + p.by - 1) / p.by;
   const int columns = p.nbx * p.nby;
-  const int req_bz = tile_req ? tile_req[2] : 0;
   p.bz = req_bz > 0 ? (req_bz < g.nz ? req_bz : g.nz) : choose_bz(g.nz, columns, p.slots, sm_count());
   p.nbz = (g.nz + p.bz - 1) / p.bz;
   int nxf = 0, nyf = 0, nzf = 0;
@@ -114,13 +135,48 @@ bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPla
   p.sz_elems = 2LL * p.nbz * nzf * int64_t(g.ny) * g.nx;
   p.parity_elems = ((p.sx_elems + p.sy_elems + p.sz_elems) + 31) / 32 * 32;
   *plan = p;
+}
+
+bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPlan* plan) {
+  const int rbx = tile_req ? tile_req[0] : 0;
+  const int rby = tile_req ? tile_req[1] : 0;
+  int rns, rwb, rnxw, rnpt;
+  pipeline_request(&rns, &rwb, &rnxw, &rnpt);
+  const K1Variant* v = find_variant(g.lattice, storage, rbx, rby, rns, rwb, rnxw, rnpt);
+  if (!v) return false;
+  fill_plan(g, v, tile_req ? tile_req[2] : 0, plan);
   return true;
+}
+
+bool k1_plan_variant(const Geometry& g, const void* variant, FusedPlan* plan) {
+  const K1Variant* v = static_cast<const K1Variant*>(variant);
+  if (!v || v->lattice != g.lattice) return false;
+  fill_plan(g, v, 0, plan);
+  return true;
+}
+
+int k1_variants_for(int lattice, int storage, const void** out, int cap) {
+  const K1Variant* lists[2];
+  int counts[2];
+  const int nl = variant_lists(lattice, lists, counts);
+  int n = 0;
+  for (int l = 0; l < nl; ++l)
+    for (int i = 0; i < counts[l]; ++i)
+      if (lists[l][i].storage == storage) {
+        if (n < cap) out[n] = &lists[l][i];
+        ++n;
+      }
+  return n;
 }
 
 static const K1Variant* ctx_variant(lb_ctx* ctx) {
   return find_variant(ctx->lattice, ctx->storage, ctx->plan.bx, ctx->plan.by, ctx->plan.slots, ctx->plan.wbuf,
-                      ctx->plan.xwarps);
+                      ctx->plan.xwarps, ctx->plan.npt);
 }
+
+const K1Variant* k1_ctx_variant(lb_ctx* ctx) { return ctx_variant(ctx); }
+
+int k1_sm_count() { return sm_count(); }
 
 cudaError_t k1_configure(lb_ctx* ctx) {
   const K1Variant* v = ctx_variant(ctx);

@@ -167,6 +167,16 @@ class Solver:
             out["residual"] = res.value
         return out
 
+    def autotune(self, steps=5):
+        """Time every compiled brick shape on a proxy of this domain and switch
+        to the fastest (lb_autotune); returns the timing table (empty when the
+        choice came from the cache)."""
+        cap = 64
+        tab = (B.lb_tune_entry * cap)()
+        n = ctypes.c_int32()
+        B.check(self._lib.lb_autotune(self._ctx, int(steps), tab, cap, ctypes.byref(n)), "lb_autotune")
+        return [{name: getattr(tab[i], name) for name, _ in tab[i]._fields_} for i in range(n.value)]
+
     def info(self) -> dict:
         inf = B.lb_info_t()
         B.check(self._lib.lb_info(self._ctx, ctypes.byref(inf)), "lb_info")
@@ -175,7 +185,50 @@ class Solver:
             "dims": tuple(inf.dims), "steps_done": inf.steps_done, "tile": tuple(inf.tile),
             "population_bytes": inf.population_bytes, "aux_bytes": inf.aux_bytes,
             "algorithmic_bytes_per_update": inf.algorithmic_bytes_per_update,
+            "nodes_per_thread": inf.nodes_per_thread, "tma_slots": inf.tma_slots,
         }
+
+
+class Batch:
+    """Many Solver domains stepped together (lb_batch_*): one persistent
+    launch per brick-shape class and time step, two steps per CUDA graph
+    replay.  The solvers must stay open while the batch exists."""
+
+    def __init__(self, solvers, stream=None):
+        self._lib = B.load()
+        self.solvers = list(solvers)
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s._ctx.value for s in self.solvers])
+        st = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream))) if stream is not None else None
+        self._b = ctypes.c_void_p()
+        B.check(self._lib.lb_batch_create(arr, len(self.solvers), st, ctypes.byref(self._b)), "lb_batch_create")
+
+    def step(self, n=1):
+        B.check(self._lib.lb_batch_step(self._b, int(n)), "lb_batch_step")
+
+    def sync(self):
+        B.check(self._lib.lb_batch_sync(self._b), "lb_batch_sync")
+
+    def info(self) -> dict:
+        inf = B.lb_batch_info_t()
+        B.check(self._lib.lb_batch_info(self._b, ctypes.byref(inf)), "lb_batch_info")
+        return {name: getattr(inf, name) for name, _ in inf._fields_}
+
+    def close(self):
+        if getattr(self, "_b", None) and self._b.value:
+            self._lib.lb_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def lattice_table(lattice):

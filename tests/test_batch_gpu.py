@@ -1,0 +1,112 @@
+"""Batched stepping (lb_batch_*) of many uneven domains.
+
+A batch runs one persistent launch per brick-shape class and time step over a
+static work list of all domains' bricks, replayed from a CUDA graph two steps
+at a time.  Every domain must come out bit for bit equal to stepping it alone
+(same per-node arithmetic, bricks and shells), for odd and even step counts,
+with members that were also stepped alone in between, and with several
+classes (lattices, storages, forcing) in one batch.  The solo path itself is
+held to the CPU oracle by the parity tests.
+"""
+import numpy as np
+import pytest
+
+import synth
+from lbcase import faces_for, random_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lb():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2304_06437_gb300 import build
+    build.build()
+    import paper_2304_06437_gb300 as P
+    return P
+
+
+def _specs(seed):
+    """Uneven domains of two lattices, random sizes, tau, boundaries, storage."""
+    g = synth.rng(seed)
+    out = []
+    for i in range(7):
+        dims = tuple(int(v) for v in g.integers(5, 48, size=3))
+        out.append(dict(lat="D3Q19", dims=dims, tau=float(g.uniform(0.55, 1.2)),
+                        fname=["periodic", "lid", "walls", "duct"][i % 4], storage="f32"))
+    for i in range(6):
+        dims = (int(g.integers(8, 300)), int(g.integers(4, 120)), 1)
+        out.append(dict(lat="D2Q9", dims=dims, tau=float(g.uniform(0.55, 1.2)),
+                        fname=["periodic", "lid"][i % 2], storage="f32"))
+    out.append(dict(lat="D3Q27", dims=(21, 13, 17), tau=0.7, fname="lid_periodic_z", storage="f32"))
+    out.append(dict(lat="D3Q19", dims=(30, 11, 9), tau=0.6, fname="duct", storage="f16s"))
+    out.append(dict(lat="D2Q9", dims=(77, 31, 1), tau=0.9, fname="lid", storage="bf16s"))
+    out.append(dict(lat="D3Q19", dims=(19, 23, 10), tau=0.8, fname="lid", storage="f64"))
+    return out
+
+
+def _make(lb, spec, seed):
+    faces, wall_u = faces_for(spec["lat"], spec["fname"])
+    force = (2e-5, 1e-5, 0.0) if spec["fname"] == "duct" else (0, 0, 0)
+    s = lb.Solver(spec["lat"], spec["dims"], spec["tau"], faces=faces, wall_u=wall_u, storage=spec["storage"],
+                  force=force)
+    s.set_populations(np.ascontiguousarray(random_state(spec["lat"], spec["dims"], seed)))
+    return s
+
+
+@pytest.mark.parametrize("steps", [1, 2, 7])
+def test_batch_equals_solo_bitwise(lb, steps):
+    specs = _specs(99)
+    solo = []
+    for i, sp in enumerate(specs):
+        s = _make(lb, sp, 500 + i)
+        s.step(steps)
+        solo.append(s.get_populations())
+        s.close()
+    members = [_make(lb, sp, 500 + i) for i, sp in enumerate(specs)]
+    with lb.Batch(members) as b:
+        info = b.info()
+        assert info["n_domains"] == len(specs)
+        assert info["n_classes"] >= 5  # D3Q19, D3Q19 forced, D2Q9, D3Q27, f16s, bf16s ...
+        b.step(steps)
+        b.sync()
+        for s, ref in zip(members, solo):
+            assert np.array_equal(s.get_populations(), ref)
+        assert info["launches_per_step"] == info["n_classes"]
+    for s in members:
+        s.close()
+
+
+def test_batch_with_members_stepped_alone(lb):
+    """Shell parities may differ between members: every other member takes a
+    solo step between two batch calls; all must equal their solo runs."""
+    specs = _specs(7)[:8]
+    solo = []
+    for i, sp in enumerate(specs):
+        s = _make(lb, sp, 900 + i)
+        s.step(3 + (1 if i % 2 == 0 else 0) + 4)
+        solo.append(s.get_populations())
+        s.close()
+    members = [_make(lb, sp, 900 + i) for i, sp in enumerate(specs)]
+    with lb.Batch(members) as b:
+        b.step(3)
+        for i, s in enumerate(members):
+            if i % 2 == 0:
+                s.step(1)  # alone, on the member's stream (which waits for the batch)
+        b.step(4)
+        b.sync()
+        for s, ref in zip(members, solo):
+            assert np.array_equal(s.get_populations(), ref)
+    for s in members:
+        s.close()
+
+
+def test_batch_rejects_unsupported(lb):
+    s2p = lb.Solver("D3Q19", (9, 9, 9), 0.7, storage="f32", scheme="two_pass")
+    s32 = lb.Solver("D3Q19", (9, 9, 9), 0.7, storage="f32")
+    for bad in ([s2p], [s32, s32], [s32, s2p]):
+        with pytest.raises(lb.LBError):
+            lb.Batch(bad)
+    for s in (s2p, s32):
+        s.close()

@@ -402,3 +402,51 @@ def test_poiseuille_parabola_second_order(lat):
     assert v16 < 1e-12 and v32 < 1e-12
     assert e32 < 5e-3
     assert 3.5 < e16 / e32 < 4.5
+
+
+# ---------------------------------------------------------------- reduced-precision storage
+def test_storage_rounding_fp16_is_ieee_binary16():
+    """Round-to-nearest-even to binary16, pinned against hand-made ties and
+    numpy's own float64 -> float16 conversion (normal and subnormal range)."""
+    from oracle.storage import quantum, round_to_format
+    ties = np.array([1 + 2.0 ** -11, 1 + 3 * 2.0 ** -11, -(1 + 2.0 ** -11), 2.0 ** -24 * 0.5, 2.0 ** -24 * 1.5,
+                     2.0 ** -14 + 2.0 ** -25, 0.0])
+    want = np.array([1.0, 1 + 2.0 ** -9, -1.0, 0.0, 2.0 ** -23, 2.0 ** -14, 0.0])
+    assert np.array_equal(round_to_format(ties, "f16s"), want)
+    g = synth.rng(5)
+    for scale in (1e-1, 3e-3, 1e-5, 1e-7):
+        x = g.uniform(-scale, scale, size=20000)
+        assert np.array_equal(round_to_format(x, "f16s"), x.astype(np.float16).astype(np.float64))
+    assert quantum(np.array([1.0, 1.5, 2.0 ** -20]), "f16s").tolist() == [2.0 ** -10, 2.0 ** -10, 2.0 ** -24]
+
+
+def test_storage_rounding_bf16_is_round_to_nearest_even():
+    """bfloat16 keeps 8 significant bits with the FP32 exponent range; pinned
+    against hand-made ties and torch's float32 -> bfloat16 conversion on
+    values that FP32 represents exactly."""
+    torch = pytest.importorskip("torch")
+    from oracle.storage import round_to_format
+    ties = np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, -(1 + 2.0 ** -8), 2.0 ** -20 * (1 + 2.0 ** -9)])
+    want = np.array([1.0, 1 + 2.0 ** -6, -1.0, 2.0 ** -20])
+    assert np.array_equal(round_to_format(ties, "bf16s"), want)
+    g = synth.rng(6)
+    for scale in (1e-1, 3e-3, 1e-5):
+        x = g.uniform(-scale, scale, size=20000).astype(np.float32)
+        ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+        assert np.array_equal(round_to_format(x.astype(np.float64), "bf16s"), ref)
+
+
+def test_stored_run_shifts_before_rounding():
+    """The reduced modes round f_a - t_a rho0, so a rest state (f = t_a rho0)
+    is stored exactly and stays at rest (up to FP64 rounding) in every format."""
+    from oracle.storage import round_populations
+    cfg = oracle.make_cfg("D3Q19", (4, 3, 5), 0.7, rho0=1.0)
+    rho, u = synth.rest_state((4, 3, 5), 3)
+    f0 = oracle.init(cfg, rho, u)
+    w = oracle.lattice_tables("D3Q19")[1]
+    for st in ("f16s", "bf16s", "f32"):
+        assert np.array_equal(round_populations(f0, w, st), f0)
+        assert np.abs(oracle.run_stored(cfg, f0, 3, st) - f0).max() < 1e-15
+    # without the shift binary16 could not hold t_a = 1/36 exactly
+    from oracle.storage import round_to_format
+    assert round_to_format(np.array([1.0 / 36.0]), "f16s")[0] != 1.0 / 36.0
