@@ -51,6 +51,11 @@ WORKLOADS = {
     # 32..1024) and 128 D3Q19 cubes (16..128), tau uniform in [0.55, 1.2], per
     # lattice half Taylor-Green (periodic) and half lid-driven cavity, FP32
     "batch_256": dict(lattice="mixed", dims=None, tau=None, flow="batch", n2d=128, n3d=128),
+    # continuous batching: Poisson arrivals (50 / s) of D3Q19 cavity and duct
+    # solves, cubes 32..256, Re 10..1000, FP32 or shifted-FP16 storage, each run
+    # until the relative velocity residual over 100 steps is below 1e-6 (cap
+    # 2e5 steps), served for a fixed wall-clock horizon
+    "serve_d3q19": dict(lattice="D3Q19", dims=None, tau=None, flow="serve", n_req=200, rate=50.0),
 }
 Q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}
@@ -265,6 +270,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving horizon (serve workload)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -272,6 +278,9 @@ def main():
         return
     if w["flow"] == "batch":
         run_batch(args, w)
+        return
+    if w["flow"] == "serve":
+        run_serve(args, w)
         return
 
     import torch
@@ -433,6 +442,23 @@ def run_batch(args, w):
     q_of = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}
     es = STORAGE_BYTES[args.storage]
     alg_bytes = sum(2 * q_of[sp["lattice"]] * es * d.n for sp, d in zip(specs, doms))
+    # the same domains one after another with their own plans, one
+    # single-domain launch per domain and step (measured before the batch
+    # re-plans its members for batched throughput)
+    seq_steps = max(2, min(args.steps, 20))
+    for d in doms:
+        d.step(1)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(seq_steps):
+        for d in doms:
+            d.step(1)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = s0.elapsed_time(s1) / seq_steps
+    seq_value = N / (seq_ms * 1e-3) / 1e6
+
     b = Batch(doms, stream=stream)
     info = b.info()
     b.step(args.warmup)
@@ -461,20 +487,6 @@ def run_batch(args, w):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
     value = ws * N * args.steps / (total_ms * 1e-3) / 1e6
-    # the same domains one after another, one single-domain launch each
-    seq_steps = max(2, min(args.steps, 20))
-    for d in doms:
-        d.step(1)
-    torch.cuda.synchronize()
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    for _ in range(seq_steps):
-        for d in doms:
-            d.step(1)
-    s1.record(stream)
-    torch.cuda.synchronize()
-    seq_ms = s0.elapsed_time(s1) / seq_steps
-    seq_value = N / (seq_ms * 1e-3) / 1e6
     b.close()
     for d in doms:
         d.close()
@@ -497,6 +509,54 @@ def run_batch(args, w):
                                     "what": "same domains, one single-domain launch per domain and step"},
             "cpu_baseline": None, "e2e": None, "clocks": clk,
             "gpu_launches": info["launches_per_step"] * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_serve(args, w):
+    """Serving workload: the request stream is replayed in real time against
+    the continuous-batching server for --serve-seconds; reports latency
+    percentiles of the requests that finished, the aggregate update rate and
+    the offered versus served load."""
+    import torch
+    from paper_2304_06437_gb300 import serve
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    reqs = serve.poisson_requests(w["n_req"], w["rate"], seed=20230412 + rank)
+    offered = sum(int(np.prod(r.dims)) for r in reqs)
+    srv = serve.Server(round_steps=100, keep_fields=False)
+    for r in reqs:
+        srv.submit(r)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    t0 = time.perf_counter()
+    srv.run(until=args.serve_seconds)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    rep = srv.report(wall)
+    srv.close()
+    if ws > 1:
+        t = torch.tensor([srv.updates / wall], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t)
+        rate = float(t.item()) / 1e6
+    else:
+        rate = srv.updates / wall / 1e6
+    if rank == 0:
+        line = {
+            "metric": "MLUPS", "value": rate, "unit": "MLUPS", "n_gpus": ws, "steps": srv.rounds * 100,
+            "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "requests": len(reqs), "rate_per_s": w["rate"],
+                       "horizon_s": args.serve_seconds, "round_steps": 100, "tol": 1e-6, "step_cap": 200000,
+                       "offered_nodes": offered, "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "serving": rep, "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk,
+            "gpu_launches": None,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -252,6 +252,11 @@ LB_API int lb_autotune(lb_ctx* ctx, int32_t steps, lb_tune_entry* table, int32_t
  * batch keeps
  * pointers to the contexts, which must outlive it and must not be re-planned
  * while it exists; stepping a member alone between batch steps is allowed.
+ * lb_batch_create re-plans members for batched throughput (kept after the
+ * batch is destroyed; results are unchanged, every plan gives the same bits):
+ * the preferred compiled brick shape that pads the domain's cross-section by
+ * at most 25 % (else the least padded one), and one brick per column for
+ * sweeps of up to 256 planes.  Classes run on parallel branches of the graph.
  * stream: cudaStream_t for the batch's work, NULL = a library-owned stream.
  * Errors: LB_E_INVAL (NULL, duplicates, mixed devices), LB_E_UNSUPPORTED,
  * LB_E_NOMEM, LB_E_CUDA. */

@@ -42,6 +42,9 @@ struct lb_batch {
   int* d_status = nullptr;
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t done = nullptr;
+  cudaEvent_t fork = nullptr;          // class branches of one step
+  std::vector<cudaStream_t> side;      // one per class after the first
+  std::vector<cudaEvent_t> join;
   std::vector<cudaEvent_t> ctx_ev;
   int64_t steps_done = 0;
   int64_t total_nodes = 0;
@@ -177,11 +180,56 @@ int setup_class(lb_batch& b, lb_batch::Class& c) {
   return LB_OK;
 }
 
+// Re-plan a member for batched throughput: the first compiled shape (in the
+// planner's order) whose bricks pad the cross-section by at most 25 %, else
+// the least padded one; and, for sweeps of up to 256 planes, one brick per
+// column, so that small domains do not pay the pipeline fill (slots + 2
+// planes) and the z-shell of short bricks.  Bits are unchanged.
+int batch_replan(lb_ctx* x) {
+  const void* vs[64];
+  const int nv = std::min(k1_variants_for(x->lattice, x->storage, vs, 64), 64);
+  const K1Variant* pick = nullptr;
+  const K1Variant* least = nullptr;
+  double least_waste = 1e300;
+  for (int i = 0; i < nv; ++i) {
+    const K1Variant* v = static_cast<const K1Variant*>(vs[i]);
+    if (!v->batched) continue;
+    const double px = double((x->g.nx + v->bx - 1) / v->bx) * v->bx;
+    const double py = double((x->g.ny + v->by - 1) / v->by) * v->by;
+    const double waste = px * py / (double(x->g.nx) * double(x->g.ny));
+    if (!pick && waste <= 1.25) pick = v;
+    if (waste < least_waste) {
+      least_waste = waste;
+      least = v;
+    }
+  }
+  if (!pick) pick = least;
+  if (!pick) return LB_E_UNSUPPORTED;
+  const int bz = x->g.nz <= 256 ? x->g.nz : 0;
+  FusedPlan want;
+  if (!k1_plan_variant(x->g, pick, bz, &want)) return LB_E_UNSUPPORTED;
+  if (pick == k1_ctx_variant(x) && want.bz == x->plan.bz) return LB_OK;
+  return ctx_replan(x, pick, bz);
+}
+
+// One step (k = 0 or 1 of the captured pair) of every class.  Classes are
+// independent domains: each runs on its own branch (the batch stream for the
+// first, a side stream forked from it for the others) and all join back.
 int launch_classes(lb_batch& b, int k) {
-  for (auto& c : b.classes) {
+  const int nc = int(b.classes.size());
+  if (nc > 1) {
+    LB_BTRY(cudaEventRecord(b.fork, b.stream));
+    for (int i = 1; i < nc; ++i) LB_BTRY(cudaStreamWaitEvent(b.side[i - 1], b.fork, 0));
+  }
+  for (int i = 0; i < nc; ++i) {
+    auto& c = b.classes[i];
     const BatchLaunch L{c.d_args, int(c.members.size()), c.d_tmaps, c.d_items, c.d_starts, c.d_par,
                         c.grid, k, c.force};
-    LB_BTRY(c.v->batched(L, b.stream));
+    LB_BTRY(c.v->batched(L, i == 0 ? b.stream : b.side[i - 1]));
+  }
+  for (int i = 1; i < nc; ++i) {
+    LB_BTRY(cudaEventRecord(b.join[i - 1], b.side[i - 1]));
+    LB_BTRY(cudaStreamWaitEvent(b.stream, b.join[i - 1], 0));
   }
   return LB_OK;
 }
@@ -236,6 +284,12 @@ int lb_batch_create(lb_ctx* const* ctxs, int32_t n, void* stream, lb_batch** out
       b->own_stream = true;
     }
     b->ctxs.assign(ctxs, ctxs + n);
+    for (int i = 0; i < n && rc == LB_OK; ++i) {
+      // the domain's own stream must be done before the batch reads its state
+      if (cudaStreamSynchronize(ctxs[i]->stream) != cudaSuccess) rc = LB_E_CUDA;
+      else rc = batch_replan(ctxs[i]);
+    }
+    if (rc != LB_OK) break;
     for (int i = 0; i < n; ++i) {
       lb_ctx* x = ctxs[i];
       b->total_nodes += x->n_nodes;
@@ -250,8 +304,6 @@ int lb_batch_create(lb_ctx* const* ctxs, int32_t n, void* stream, lb_batch** out
         it = b->classes.end() - 1;
       }
       it->members.push_back(i);
-      // the domain's own stream must be done before the batch reads its state
-      if (cudaStreamSynchronize(x->stream) != cudaSuccess) { rc = LB_E_CUDA; break; }
     }
     if (rc != LB_OK) break;
     if (cudaMalloc(reinterpret_cast<void**>(&b->d_status), sizeof(int)) != cudaSuccess) { rc = LB_E_NOMEM; break; }
@@ -262,6 +314,16 @@ int lb_batch_create(lb_ctx* const* ctxs, int32_t n, void* stream, lb_batch** out
     }
     if (rc != LB_OK) break;
     if (cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) { rc = LB_E_CUDA; break; }
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) { rc = LB_E_CUDA; break; }
+    for (size_t i = 1; i < b->classes.size() && rc == LB_OK; ++i) {
+      cudaStream_t st = nullptr;
+      cudaEvent_t ev = nullptr;
+      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) rc = LB_E_CUDA;
+      else b->side.push_back(st);
+      if (rc == LB_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) rc = LB_E_CUDA;
+      else if (rc == LB_OK) b->join.push_back(ev);
+    }
+    if (rc != LB_OK) break;
     b->ctx_ev.resize(n, nullptr);
     for (int i = 0; i < n && rc == LB_OK; ++i)
       if (cudaEventCreateWithFlags(&b->ctx_ev[i], cudaEventDisableTiming) != cudaSuccess) rc = LB_E_CUDA;
@@ -349,6 +411,11 @@ void lb_batch_destroy(lb_batch* b) {
   for (auto& c : b->classes) free_class(c);
   if (b->d_status) cudaFree(b->d_status);
   if (b->done) cudaEventDestroy(b->done);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t st : b->side)
+    if (st) cudaStreamDestroy(st);
   for (cudaEvent_t e : b->ctx_ev)
     if (e) cudaEventDestroy(e);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);

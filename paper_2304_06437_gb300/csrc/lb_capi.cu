@@ -131,10 +131,10 @@ struct DeviceGuard {
 
 namespace lbgb {
 
-int ctx_replan(lb_ctx* ctx, const void* variant) {
+int ctx_replan(lb_ctx* ctx, const void* variant, int bz) {
   if (!ctx || ctx->scheme != LB_SCHEME_FUSED) return LB_E_INVAL;
   FusedPlan p;
-  if (!k1_plan_variant(ctx->g, variant, &p)) return LB_E_INVAL;
+  if (!k1_plan_variant(ctx->g, variant, bz, &p)) return LB_E_INVAL;
   DeviceGuard guard(ctx->device);
   LB_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
   const size_t aux_bytes = size_t(2) * size_t(p.parity_elems) * ctx->real_bytes;

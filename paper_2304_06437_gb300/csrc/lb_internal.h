@@ -80,13 +80,15 @@ cudaError_t k0_step_buffers(const Geometry& g, double* ft, double* mom, cudaStre
 
 // ---- fused scheme (lb_k1_*.cu)
 bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPlan* plan);
-// plan with one given compiled shape (a K1Variant*, see lb_k1_launch.cuh)
-bool k1_plan_variant(const Geometry& g, const void* variant, FusedPlan* plan);
+// plan with one given compiled shape (a K1Variant*, see lb_k1_launch.cuh) and
+// sweep length bz (0 = the planner's choice)
+bool k1_plan_variant(const Geometry& g, const void* variant, int bz, FusedPlan* plan);
 // compiled shapes for (lattice, storage), in the planner's order; returns the count
 int k1_variants_for(int lattice, int storage, const void** out, int cap);
-// switch a fused-scheme context to another compiled shape: new shell buffers
-// and TMA descriptor, shell rebuilt from the current populations (lb_capi.cu)
-int ctx_replan(lb_ctx* ctx, const void* variant);
+// switch a fused-scheme context to another compiled shape and sweep length
+// (bz = 0: the planner's choice): new shell buffers and TMA descriptor, shell
+// rebuilt from the current populations (lb_capi.cu)
+int ctx_replan(lb_ctx* ctx, const void* variant, int bz = 0);
 cudaError_t k1_step(lb_ctx* ctx);
 cudaError_t k1_bootstrap(lb_ctx* ctx);  // fill the current shell parity from f
 cudaError_t k1_configure(lb_ctx* ctx);  // one-time kernel attributes

@@ -8,8 +8,10 @@ namespace lbgb {
 
 extern const K1Variant k1_variants_d2q9[] = {
     K1Impl<D2Q9, float, float, 256,1,4,2,0>::variant(LB_D2Q9, LB_F32),
+    K1Impl<D2Q9, float, float, 64,1,4,2,0>::variant(LB_D2Q9, LB_F32),   // narrow domains (batches)
     K1Impl<D2Q9, double, double, 256,1,3,2,0>::variant(LB_D2Q9, LB_F64),
     K1Impl<D2Q9, __half, float, 256,1,4,2,0>::variant(LB_D2Q9, LB_F16S),
+    K1Impl<D2Q9, __half, float, 64,1,4,2,0>::variant(LB_D2Q9, LB_F16S),
     K1Impl<D2Q9, __nv_bfloat16, float, 256,1,4,2,0>::variant(LB_D2Q9, LB_BF16S),
 };
 extern const int k1_n_variants_d2q9 = sizeof(k1_variants_d2q9) / sizeof(k1_variants_d2q9[0]);

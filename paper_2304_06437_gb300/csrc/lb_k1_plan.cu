@@ -148,10 +148,10 @@ bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPla
   return true;
 }
 
-bool k1_plan_variant(const Geometry& g, const void* variant, FusedPlan* plan) {
+bool k1_plan_variant(const Geometry& g, const void* variant, int bz, FusedPlan* plan) {
   const K1Variant* v = static_cast<const K1Variant*>(variant);
   if (!v || v->lattice != g.lattice) return false;
-  fill_plan(g, v, 0, plan);
+  fill_plan(g, v, bz, plan);
   return true;
 }
 
