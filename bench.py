@@ -161,6 +161,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x, torch):
+    """The largest value over the ranks of the default process group (the
+    value itself without one): the job's time is its slowest rank's."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, torch):
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -324,11 +346,7 @@ def main():
     clk = clocks.stop()
     barrier()
     per_launch = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[args.steps])
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(ev[0].elapsed_time(ev[args.steps]), torch)
     value = ws * N * args.steps / (total_ms * 1e-3) / 1e6
     ms_per_step = total_ms / args.steps
     launches_per_step = 1 if args.scheme == "fused" else 2
@@ -481,11 +499,7 @@ def run_batch(args, w):
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier()
-    total_ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(e0.elapsed_time(e1), torch)
     value = ws * N * args.steps / (total_ms * 1e-3) / 1e6
     b.close()
     for d in doms:
@@ -541,12 +555,7 @@ def run_serve(args, w):
     clk = clocks.stop()
     rep = srv.report(wall)
     srv.close()
-    if ws > 1:
-        t = torch.tensor([srv.updates / wall], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t)
-        rate = float(t.item()) / 1e6
-    else:
-        rate = srv.updates / wall / 1e6
+    rate = sum_over_ranks(srv.updates / wall, torch) / 1e6
     if rank == 0:
         line = {
             "metric": "MLUPS", "value": rate, "unit": "MLUPS", "n_gpus": ws, "steps": srv.rounds * 100,
