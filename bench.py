@@ -293,6 +293,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving horizon (serve workload)")
+    ap.add_argument("--serve-max-nodes", type=int, default=1 << 26, help="cap on resident nodes (serve workload)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -543,7 +544,7 @@ def run_serve(args, w):
     torch.cuda.set_device(local)
     reqs = serve.poisson_requests(w["n_req"], w["rate"], seed=20230412 + rank)
     offered = sum(int(np.prod(r.dims)) for r in reqs)
-    srv = serve.Server(round_steps=100, keep_fields=False)
+    srv = serve.Server(round_steps=100, keep_fields=False, max_active_nodes=args.serve_max_nodes, order="smallest")
     for r in reqs:
         srv.submit(r)
     clocks = ClockSampler(torch.cuda.current_device())
@@ -563,6 +564,7 @@ def run_serve(args, w):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "requests": len(reqs), "rate_per_s": w["rate"],
                        "horizon_s": args.serve_seconds, "round_steps": 100, "tol": 1e-6, "step_cap": 200000,
+                       "admission": "smallest first, free HBM, at most %d resident nodes" % args.serve_max_nodes,
                        "offered_nodes": offered, "parallelism": "replicas" if ws > 1 else "single GPU"},
             "serving": rep, "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk,
             "gpu_launches": None,

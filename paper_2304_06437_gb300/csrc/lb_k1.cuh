@@ -118,10 +118,15 @@ struct K1Shape {
   static constexpr size_t WIN = size_t(NLAT) * WPLANE * sizeof(R);
   static constexpr size_t STAGE = size_t(QP) * PMAX * sizeof(R);
   static constexpr size_t OFF_WIN = align128(NS * SLOT);
+  // with dedicated export warps the lateral export runs decoupled from the
+  // node warps' per-plane barrier, through a ring of SR staged planes
+  // guarded by full / empty mbarriers; otherwise two staged planes suffice
+  static constexpr bool DEC = NXW > 0;
+  static constexpr int SR = DEC ? 4 : 2;
   static constexpr size_t OFF_STAGE = OFF_WIN + WB * align128(WIN);
-  static constexpr size_t OFF_DESC = OFF_STAGE + align128(2 * STAGE);
+  static constexpr size_t OFF_DESC = OFF_STAGE + align128(SR * STAGE);
   static constexpr size_t OFF_BAR = OFF_DESC + align128(size_t(PMAX) * 24);
-  static constexpr size_t SMEM = OFF_BAR + align128(NS * sizeof(uint64_t));
+  static constexpr size_t SMEM = OFF_BAR + align128((NS + 2 * SR) * sizeof(uint64_t));
   static_assert(BY == 1 || NYF > 0, "a 2D brick has one internal row");
   static_assert(NXW > 0 || PMAX <= NTM, "perimeter larger than the CTA");
   static_assert(WB == 1 || WB == 2, "one or two window buffers");
@@ -325,12 +330,28 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   const R* __restrict__ shc = args.sh_cur;
 
   // ---------------------------------------------------------------- setup
+  constexpr bool DEC = Sh::DEC;
+  constexpr int SR = Sh::SR;
+  uint64_t* sfull = bars + NS;        // staged plane ready (node threads arrive)
+  uint64_t* sempty = bars + NS + SR;  // staged plane exported (export threads arrive)
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+    if constexpr (DEC) {
+      for (int s = 0; s < SR; ++s) {
+        mbar_init(&sfull[s], NTM);
+        mbar_init(&sempty[s], 32 * NXW);
+      }
+    }
     fence_barrier_init();
     prefetch_tmap(tmap_p);
   }
   __syncthreads();
+  // the node threads' per-plane barrier: the whole CTA, or only the node
+  // warps when dedicated export warps run decoupled
+  auto node_sync_or = [&](bool pred) -> bool {
+    if constexpr (DEC) return bar_red_or(1, NTM, pred);
+    else return __syncthreads_or(pred);
+  };
   int issued = 0;  // real planes whose load was issued (thread 0's view)
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) {
@@ -449,12 +470,12 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   }
   // (the first barrier of the sweep orders these writes before their use)
 
-  auto export_staged = [&](int zx) {
+  auto export_staged = [&](int zx, int sslot) {
     if (exp_warp && zx >= z0 && zx < z1) {
       R* shn = args.sh_next;
 #pragma unroll 1
       for (int p = exp_lane; p < pcount; p += 32 * Sh::NEXW) {
-        const Vec* st = reinterpret_cast<const Vec*>(stage + (zx & 1) * (QP * PMAX) + p * QP);
+        const Vec* st = reinterpret_cast<const Vec*>(stage + sslot * (QP * PMAX) + p * QP);
         R fin[QP];
 #pragma unroll
         for (int v = 0; v < QP / VEC; ++v) *reinterpret_cast<Vec*>(&fin[v * VEC]) = st[v];
@@ -548,153 +569,174 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
     }
   };
 
-  // ------------------------------------------------ prologue: plane z0 - 1
-  R onl_g[3] = {R(0), R(0), R(0)};  // non-lateral populations of the gathered plane
-  {
-    bool ok = produce(z0 - 1, win0 + ((z0 - 1) & 1) * WSTRIDE, onl_g);
-    if (is_main) LB_RING_PUT(win0 + ((z0 - 1) & 1) * WSTRIDE, z0 - 1);
-    if (__syncthreads_or(!ok)) {
-      abort_cta(0);
-      return false;
+  if (DEC && !is_main) {
+    // dedicated export warps: export each staged plane as soon as the node
+    // threads mark it ready, then hand the ring slot back
+#pragma unroll 1
+    for (int zx = z0; zx < z1; ++zx) {
+      const int sl = (zx - z0) % SR;
+      if (!mbar_wait_bounded(&sfull[sl], ((zx - z0) / SR) & 1, kWaitLimitNs)) {
+        atomicExch(args.status, LB_E_TIMEOUT);
+        return false;
+      }
+      export_staged(zx, sl);
+      mbar_arrive(&sempty[sl]);
     }
-  }
-#pragma unroll
-  for (int e = 0; e < HPT; ++e) ha[e] = hb[e];
-  halo_fetch(hb, z0 + 1);
-
-  // ------------------------------------------------ sweep: gather plane g,
-  // produce plane g + 1 in the same barrier interval (independent work)
-  for (int g = z0 - 1; g <= z1; ++g) {
-    const int c = g + 1;
-    R* win_g = win0 + (g & 1) * WSTRIDE;
-    R* win_c = win0 + (c & 1) * WSTRIDE;
-    const bool real_g = g >= z0 && g < z1;
-    const bool need_g = plane_needed(g);
-
-    R onl_c[3] = {R(0), R(0), R(0)};
-    bool ok = true;
-    if (c <= z1) {
-      ok = produce(c, win_c, onl_c);
-      if (is_main) LB_RING_PUT(win_c, c);
+  } else {
+    // ------------------------------------------------ prologue: plane z0 - 1
+    R onl_g[3] = {R(0), R(0), R(0)};  // non-lateral populations of the gathered plane
+    {
+      bool ok = produce(z0 - 1, win0 + ((z0 - 1) & 1) * WSTRIDE, onl_g);
+      if (is_main) LB_RING_PUT(win0 + ((z0 - 1) & 1) * WSTRIDE, z0 - 1);
+      if (node_sync_or(!ok)) {
+        abort_cta(0);
+        return false;
+      }
     }
+  #pragma unroll
+    for (int e = 0; e < HPT; ++e) ha[e] = hb[e];
+    halo_fetch(hb, z0 + 1);
 
-    // gather plane g (window complete since the previous barrier)
-    if (active && need_g) {
-      static_for<0, Q>([&](auto A_) {
-        constexpr int a = decltype(A_)::value;
-        constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
-        R v;
-        if constexpr (is_lateral<L>(a)) v = win_g[lat_index<L>(a) * WPLANE + wbase - cy * WX - cx];
-        else v = onl_g[a == 0 ? 0 : (cz == 1 ? 1 : 2)];
-        if constexpr (cz == -1) G0[a] = v;
-        if constexpr (cz == 0) G1[a] = v;
-        if constexpr (cz == 1) G2[a] = v;
-      });
-    }
-    // exports of plane g - 2 (staged one iteration ago)
-    export_staged(g - 2);
+    // ------------------------------------------------ sweep: gather plane g,
+    // produce plane g + 1 in the same barrier interval (independent work)
+    for (int g = z0 - 1; g <= z1; ++g) {
+      const int c = g + 1;
+      R* win_g = win0 + (g & 1) * WSTRIDE;
+      R* win_c = win0 + (c & 1) * WSTRIDE;
+      const bool real_g = g >= z0 && g < z1;
+      const bool need_g = plane_needed(g);
 
-    // z-descending bounce-backs of plane g - 1, saved one plane ago
-    if (bdn_mask) {
-      static_for<0, Q>([&](auto A_) {
-        constexpr int a = decltype(A_)::value;
-        if constexpr (L::cz(a) == -1) {
-          constexpr int i = sub_index<L>(2, -1, a);
-          if (bdn_mask >> i & 1) G0[a] = bdn[i];
-        }
-      });
-      bdn_mask = 0;
-    }
-    // halfway bounce-back for destination plane g (threads next to a wall)
-    if (real_g && active && (xy_wall || (z_walls && (g == 0 || g == nz - 1)))) {
-      const bool bzlo = z_walls && g == 0, bzhi = z_walls && g == nz - 1;
-      static_for<0, Q>([&](auto A_) {
-        constexpr int a = decltype(A_)::value;
-        constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
-        int cb = 0;
-        if constexpr (cx == 1) cb |= bxlo ? 1 : 0;
-        if constexpr (cx == -1) cb |= bxhi ? 1 : 0;
-        if constexpr (cy == 1) cb |= bylo ? 2 : 0;
-        if constexpr (cy == -1) cb |= byhi ? 2 : 0;
-        if constexpr (cz == 1) cb |= bzlo ? 4 : 0;
-        if constexpr (cz == -1) cb |= bzhi ? 4 : 0;
-        if (cb != 0) {
-          constexpr int oa = L::opp(a);
-          R back;
-          if constexpr (is_lateral<L>(oa)) back = win_g[lat_index<L>(oa) * WPLANE + wbase];
-          else back = onl_g[oa == 0 ? 0 : (L::cz(oa) == 1 ? 1 : 2)];
-          const R v = back + args.bb[a][cb];
-          if constexpr (cz == -1) {
+      R onl_c[3] = {R(0), R(0), R(0)};
+      bool ok = true;
+      if (c <= z1) {
+        ok = produce(c, win_c, onl_c);
+        if (is_main) LB_RING_PUT(win_c, c);
+      }
+
+      // gather plane g (window complete since the previous barrier)
+      if (active && need_g) {
+        static_for<0, Q>([&](auto A_) {
+          constexpr int a = decltype(A_)::value;
+          constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+          R v;
+          if constexpr (is_lateral<L>(a)) v = win_g[lat_index<L>(a) * WPLANE + wbase - cy * WX - cx];
+          else v = onl_g[a == 0 ? 0 : (cz == 1 ? 1 : 2)];
+          if constexpr (cz == -1) G0[a] = v;
+          if constexpr (cz == 0) G1[a] = v;
+          if constexpr (cz == 1) G2[a] = v;
+        });
+      }
+      // exports of plane g - 2 (staged one iteration ago)
+      if constexpr (!DEC) export_staged(g - 2, (g - 2) & 1);
+
+      // z-descending bounce-backs of plane g - 1, saved one plane ago
+      if (bdn_mask) {
+        static_for<0, Q>([&](auto A_) {
+          constexpr int a = decltype(A_)::value;
+          if constexpr (L::cz(a) == -1) {
             constexpr int i = sub_index<L>(2, -1, a);
-            bdn[i] = v;
-            bdn_mask |= 1u << i;
-          } else {
-            G1[a] = v;
+            if (bdn_mask >> i & 1) G0[a] = bdn[i];
+          }
+        });
+        bdn_mask = 0;
+      }
+      // halfway bounce-back for destination plane g (threads next to a wall)
+      if (real_g && active && (xy_wall || (z_walls && (g == 0 || g == nz - 1)))) {
+        const bool bzlo = z_walls && g == 0, bzhi = z_walls && g == nz - 1;
+        static_for<0, Q>([&](auto A_) {
+          constexpr int a = decltype(A_)::value;
+          constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+          int cb = 0;
+          if constexpr (cx == 1) cb |= bxlo ? 1 : 0;
+          if constexpr (cx == -1) cb |= bxhi ? 1 : 0;
+          if constexpr (cy == 1) cb |= bylo ? 2 : 0;
+          if constexpr (cy == -1) cb |= byhi ? 2 : 0;
+          if constexpr (cz == 1) cb |= bzlo ? 4 : 0;
+          if constexpr (cz == -1) cb |= bzhi ? 4 : 0;
+          if (cb != 0) {
+            constexpr int oa = L::opp(a);
+            R back;
+            if constexpr (is_lateral<L>(oa)) back = win_g[lat_index<L>(oa) * WPLANE + wbase];
+            else back = onl_g[oa == 0 ? 0 : (L::cz(oa) == 1 ? 1 : 2)];
+            const R v = back + args.bb[a][cb];
+            if constexpr (cz == -1) {
+              constexpr int i = sub_index<L>(2, -1, a);
+              bdn[i] = v;
+              bdn_mask |= 1u << i;
+            } else {
+              G1[a] = v;
+            }
+          }
+        });
+      }
+
+      // plane g - 1 is complete: store, stage its perimeter, export along z
+      const int zd = g - 1;
+      if (active && zd >= z0 && zd < z1) {
+        S* p = fglob + (x + args.pitch * (y + int64_t(ny) * zd));
+        static_for<0, Q>([&](auto A_) {
+          constexpr int a = decltype(A_)::value;
+          *p = store_as<S, R>(G0[a]);
+          p += args.vol;
+        });
+        if (pidx >= 0 && any_lateral_export) {
+          const int sslot = DEC ? (zd - z0) % SR : (zd & 1);
+          // the export warps must be done with this ring slot's previous plane
+          if (DEC && zd - z0 >= SR && !mbar_wait_bounded(&sempty[sslot], (((zd - z0) / SR) - 1) & 1, kWaitLimitNs))
+            ok = false;
+          Vec* st = reinterpret_cast<Vec*>(stage + sslot * (QP * PMAX) + pidx * QP);
+  #pragma unroll
+          for (int v = 0; v < QP / VEC; ++v) {
+            R tmp[VEC];
+  #pragma unroll
+            for (int j = 0; j < VEC; ++j) tmp[j] = (v * VEC + j < Q) ? G0[(v * VEC + j) < Q ? v * VEC + j : 0] : R(0);
+            st[v] = *reinterpret_cast<const Vec*>(tmp);
           }
         }
-      });
-    }
-
-    // plane g - 1 is complete: store, stage its perimeter, export along z
-    const int zd = g - 1;
-    if (active && zd >= z0 && zd < z1) {
-      S* p = fglob + (x + args.pitch * (y + int64_t(ny) * zd));
-      static_for<0, Q>([&](auto A_) {
-        constexpr int a = decltype(A_)::value;
-        *p = store_as<S, R>(G0[a]);
-        p += args.vol;
-      });
-      if (pidx >= 0 && any_lateral_export) {
-        Vec* st = reinterpret_cast<Vec*>(stage + (zd & 1) * (QP * PMAX) + pidx * QP);
-#pragma unroll
-        for (int v = 0; v < QP / VEC; ++v) {
-          R tmp[VEC];
-#pragma unroll
-          for (int j = 0; j < VEC; ++j) tmp[j] = (v * VEC + j < Q) ? G0[(v * VEC + j) < Q ? v * VEC + j : 0] : R(0);
-          st[v] = *reinterpret_cast<const Vec*>(tmp);
-        }
+        const bool eD = zd == z0 && nbD, eU = zd == z1 - 1 && nbU;
+        if (eD || eU) export_node<L, S, R, FORCE>(args, G0, x, y, zd, (eD ? kFaceD : 0u) | (eU ? kFaceU : 0u), bI, bJ, bK);
       }
-      const bool eD = zd == z0 && nbD, eU = zd == z1 - 1 && nbU;
-      if (eD || eU) export_node<L, S, R, FORCE>(args, G0, x, y, zd, (eD ? kFaceD : 0u) | (eU ? kFaceU : 0u), bI, bJ, bK);
+      // every node thread (staging or not) marks the staged plane ready
+      if (DEC && zd >= z0 && zd < z1) mbar_arrive(&sfull[(zd - z0) % SR]);
+
+      // ring values move up one plane; start the loads two planes ahead
+  #pragma unroll
+      for (int e = 0; e < HPT; ++e) ha[e] = hb[e];
+      halo_fetch(hb, c + 2);
+
+      // rotate: plane g's partial set becomes the "previous" plane
+  #pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        G0[a] = G1[a];
+        G1[a] = G2[a];
+      }
+      onl_g[0] = onl_c[0];
+      onl_g[1] = onl_c[1];
+      onl_g[2] = onl_c[2];
+
+      // the only barrier of the iteration: plane c's window is complete and
+      // every thread has left plane g's buffers, which plane c + 1 reuses
+      if (node_sync_or(!ok)) {
+        abort_cta(c - z0);
+        return false;
+      }
+      // refill the slot consumed by plane c with plane c + NS
+      if (tid == 0 && c >= z0 && c < z1 && c + NS < z1) {
+        const int slot = (c - z0) % NS;
+        mbar_arrive_expect_tx(&bars[slot], static_cast<uint32_t>(Sh::SLOT));
+        tma_load_4d(slots + size_t(slot) * Q * BY * BX, tmap_p, x0, y0, c + NS, 0, &bars[slot]);
+        ++issued;
+      }
     }
 
-    // ring values move up one plane; start the loads two planes ahead
-#pragma unroll
-    for (int e = 0; e < HPT; ++e) ha[e] = hb[e];
-    halo_fetch(hb, c + 2);
-
-    // rotate: plane g's partial set becomes the "previous" plane
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
-      G0[a] = G1[a];
-      G1[a] = G2[a];
-    }
-    onl_g[0] = onl_c[0];
-    onl_g[1] = onl_c[1];
-    onl_g[2] = onl_c[2];
-
-    // the only barrier of the iteration: plane c's window is complete and
-    // every thread has left plane g's buffers, which plane c + 1 reuses
-    if (__syncthreads_or(!ok)) {
-      abort_cta(c - z0);
-      return false;
-    }
-    // refill the slot consumed by plane c with plane c + NS
-    if (tid == 0 && c >= z0 && c < z1 && c + NS < z1) {
-      const int slot = (c - z0) % NS;
-      mbar_arrive_expect_tx(&bars[slot], static_cast<uint32_t>(Sh::SLOT));
-      tma_load_4d(slots + size_t(slot) * Q * BY * BX, tmap_p, x0, y0, c + NS, 0, &bars[slot]);
-      ++issued;
-    }
+    // exports of the last two planes
+    if constexpr (!DEC) export_staged(z1 - 1, (z1 - 1) & 1);
   }
-
-  // exports of the last two planes
-  export_staged(z1 - 1);
   // every issued plane has been waited for: retire the barriers so that the
   // next brick of a persistent CTA can initialise them again
   __syncthreads();
   if (tid == 0)
-    for (int s = 0; s < NS; ++s) mbar_inval(&bars[s]);
+    for (int s = 0; s < NS + (DEC ? 2 * SR : 0); ++s) mbar_inval(&bars[s]);
   __syncthreads();
   return true;
 #undef LB_RING_PUT

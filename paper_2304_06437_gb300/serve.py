@@ -11,9 +11,10 @@ brick-shape class and step, CUDA-graph replays).  Between rounds it
   ||u_t - u_{t-K}|| / ||u_t|| (``lb_reduce``; K = round_steps) and retires the
   domains that converged or hit their step cap (their rho and u are copied to
   the host and their device memory freed);
-* admits queued requests, first come first served, while the device's free
-  memory minus a reserve covers the request's estimated footprint, so
-  requests that arrive while others run join the next round;
+* admits arrived requests (first come first served, or smallest first) while
+  the device's free memory minus a reserve covers the request's estimated
+  footprint and an optional cap on resident nodes allows, so requests that
+  arrive while others run join the next round;
 * rebuilds the batch when its membership changed.
 
 Every domain takes whole rounds from its own admission, so its step count
@@ -80,7 +81,8 @@ class Server:
     """
 
     def __init__(self, round_steps: int = 100, reserve_bytes: int = 2 << 30, clock: Optional[Callable[[], float]] = None,
-                 free_bytes: Optional[Callable[[], int]] = None, keep_fields: bool = True, stream=None):
+                 free_bytes: Optional[Callable[[], int]] = None, keep_fields: bool = True, stream=None,
+                 max_active_nodes: Optional[int] = None, order: str = "fifo"):
         import torch
         self.torch = torch
         self.round_steps = int(round_steps)
@@ -90,6 +92,13 @@ class Server:
         self.free_bytes = free_bytes or (lambda: torch.cuda.mem_get_info()[0])
         self.keep_fields = keep_fields
         self.stream = stream
+        # admission policy: a cap on resident nodes keeps rounds short under
+        # overload; "smallest" admits the smallest arrived request first
+        # (shortest-job-first by size), "fifo" in arrival order
+        self.max_active_nodes = max_active_nodes
+        if order not in ("fifo", "smallest"):
+            raise ValueError("order must be 'fifo' or 'smallest'")
+        self.order = order
         self.queue: List[Request] = []
         self.active: List[tuple] = []       # (request, solver)
         self.done: List[Request] = []
@@ -105,12 +114,22 @@ class Server:
     def _admit(self) -> bool:
         changed = False
         now = self.clock()
-        while self.queue and self.queue[0].arrival <= now:
-            req = self.queue[0]
+        while True:
+            arrived = [i for i, r in enumerate(self.queue) if r.arrival <= now]
+            if not arrived:
+                break
+            if self.order == "smallest":
+                pick = min(arrived, key=lambda i: (int(np.prod(self.queue[i].dims)), self.queue[i].arrival))
+            else:
+                pick = arrived[0]
+            req = self.queue[pick]
             need = footprint_bytes(req)
-            if self.free_bytes() - need < self.reserve and self.active:
-                break  # wait for memory; an empty server always admits the head
-            self.queue.pop(0)
+            if self.active and self.free_bytes() - need < self.reserve:
+                break  # wait for memory; an empty server always admits
+            if (self.active and self.max_active_nodes is not None and
+                    sum(s.n for _, s in self.active) + int(np.prod(req.dims)) > self.max_active_nodes):
+                break
+            self.queue.pop(pick)
             s = Solver(req.lattice, req.dims, req.tau, faces=req.faces, wall_u=req.wall_u, force=req.force,
                        storage=req.storage, stream=self.stream)
             s.reduce(residual=True)  # residual baseline: u at admission
