@@ -285,6 +285,16 @@ LB_API int lb_batch_info(const lb_batch* b, lb_batch_info_t* info);
 /* Frees the batch (not its contexts).  NULL is allowed. */
 LB_API void lb_batch_destroy(lb_batch* b);
 
+/* Self-test of the bounded wait that every kernel applies to its mbarrier
+ * waits (the paper has no counterpart: failure detection of this library).
+ * Launches one tiny kernel that waits on a barrier nothing completes, for at
+ * most limit_ns nanoseconds (0 .. 5e9), and returns the status the kernel
+ * recorded -- LB_E_TIMEOUT when the wait ran out as designed -- with the time
+ * it waited in *waited_ns (may be NULL).  Uses the current device and the
+ * default stream; synchronises the device.  Errors: LB_E_INVAL, LB_E_NOMEM,
+ * LB_E_CUDA. */
+LB_API int lb_selftest_timeout(int64_t limit_ns, int64_t* waited_ns);
+
 /* Human-readable name of a status code. */
 LB_API const char* lb_status_string(int code);
 

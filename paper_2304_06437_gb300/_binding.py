@@ -140,6 +140,7 @@ SIGNATURES = {
     "lb_batch_sync": (ctypes.c_int, [_vp]),
     "lb_batch_info": (ctypes.c_int, [_vp, _P(lb_batch_info_t)]),
     "lb_batch_destroy": (None, [_vp]),
+    "lb_selftest_timeout": (ctypes.c_int, [ctypes.c_int64, _i64p]),
     "lb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lb_abi_version": (ctypes.c_int, []),
 }
