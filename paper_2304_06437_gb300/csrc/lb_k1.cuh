@@ -371,7 +371,9 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   bool hval[HPT];
 #pragma unroll
   for (int e = 0; e < HPT; ++e) {
-    const int h = is_main ? tid + e * NTM : H;
+    // later rounds of ring entries go to the last threads, away from the
+    // export warps at the front of the CTA
+    const int h = is_main ? (e == 0 ? tid : (NTM - 1 - tid) + e * NTM) : H;
     hval[e] = false;
     hbase[e] = 0;
     hzs[e] = 1;
@@ -444,8 +446,11 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   const int pidx = active ? perimeter_index<NYF>(tx, ty, bxa, bya) : -1;
   const int pcount = perimeter_count<NYF>(bxa, bya);
   const bool any_lateral_export = nbW || nbE || (NYF > 0 && (nbS || nbN));
-  const bool exp_warp = any_lateral_export && (NXW > 0 ? !is_main : warp < NEXW);
-  const int exp_lane = NXW > 0 ? tid - NTM : warp * 32 + lane;  // first perimeter node of this lane
+  // shared export warps start at warp EXW0: past the first brick row, whose
+  // warps also stage a whole row of perimeter nodes every plane
+  constexpr int EXW0 = (NXW == 0 && NTM / 32 >= NEXW + 4 && BY >= 4) ? 2 : 0;
+  const bool exp_warp = any_lateral_export && (NXW > 0 ? !is_main : (warp >= EXW0 && warp < EXW0 + NEXW));
+  const int exp_lane = NXW > 0 ? tid - NTM : (warp - EXW0) * 32 + lane;  // first perimeter node of this lane
 
   // this thread's own cell in the window (interior of the padding ring)
   const int wbase = (ty + PY) * WX + (tx + 1);

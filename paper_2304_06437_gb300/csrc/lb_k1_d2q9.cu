@@ -1,7 +1,8 @@
 // lb_k1_d2q9.cu -- compiled brick shapes of the fused step for D2Q9.
 // Each entry: storage / arithmetic type, brick bx x by, TMA pipeline depth,
-// window buffers, dedicated export warps.  The first entry of a storage type
-// is the default; the others are alternatives the planner can be asked for.
+// window buffers, dedicated export warps.  For D2Q9 the paired shapes of
+// lb_k2_d2q9.cu come first in the planner's order; these are alternatives
+// (the narrow 64 x 1 brick serves small domains in batches).
 #include "lb_k1_launch.cuh"
 
 namespace lbgb {

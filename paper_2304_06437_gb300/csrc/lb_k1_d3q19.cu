@@ -1,7 +1,8 @@
 // lb_k1_d3q19.cu -- compiled brick shapes of the fused step for D3Q19.
 // Each entry: storage / arithmetic type, brick bx x by, TMA pipeline depth,
 // window buffers, dedicated export warps.  The first entry of a storage type
-// is the default; the others are alternatives the planner can be asked for.
+// is the default; the others are alternatives the planner can be asked for
+// (by brick shape, LB_FUSED_PIPELINE, the autotuner or a batch).
 #include "lb_k1_launch.cuh"
 
 namespace lbgb {
@@ -9,6 +10,7 @@ namespace lbgb {
 extern const K1Variant k1_variants_d3q19[] = {
     K1Impl<D3Q19, float, float, 64,8,3,2,0>::variant(LB_D3Q19, LB_F32),
     K1Impl<D3Q19, float, float, 64,7,3,2,2>::variant(LB_D3Q19, LB_F32),    // + 2 decoupled export warps
+    K1Impl<D3Q19, float, float, 64,6,3,2,4>::variant(LB_D3Q19, LB_F32),    // + 4 decoupled export warps
     K1Impl<D3Q19, float, float, 32,8,2,2,0>::variant(LB_D3Q19, LB_F32),  // small domains (batches)
     K1Impl<D3Q19, double, double, 32,8,2,2,0>::variant(LB_D3Q19, LB_F64),
     K1Impl<D3Q19, __half, float, 64,8,4,2,0>::variant(LB_D3Q19, LB_F16S),

@@ -1,7 +1,8 @@
 // lb_k1_d3q27.cu -- compiled brick shapes of the fused step for D3Q27.
 // Each entry: storage / arithmetic type, brick bx x by, TMA pipeline depth,
 // window buffers, dedicated export warps.  The first entry of a storage type
-// is the default; the others are alternatives the planner can be asked for.
+// is the default; the others are alternatives the planner can be asked for
+// (by brick shape, LB_FUSED_PIPELINE, the autotuner or a batch).
 #include "lb_k1_launch.cuh"
 
 namespace lbgb {

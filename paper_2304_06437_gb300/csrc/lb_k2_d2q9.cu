@@ -1,7 +1,7 @@
 // lb_k2_d2q9.cu -- compiled brick shapes of the paired (two nodes per thread,
 // FP32x2 arithmetic) fused step for D2Q9.  Each entry: storage type, brick
-// bx x by, TMA pipeline depth.  These come before the scalar shapes of
-// lb_k1_d2q9.cu when the planner picks a default for a storage type.
+// bx x by, TMA pipeline depth.  For D2Q9 these come first in the planner's
+// order (the default), before the scalar shapes of lb_k1_d2q9.cu.
 #include "lb_k2.cuh"
 
 namespace lbgb {

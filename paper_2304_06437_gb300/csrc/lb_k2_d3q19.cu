@@ -1,7 +1,7 @@
 // lb_k2_d3q19.cu -- compiled brick shapes of the paired (two nodes per thread,
 // FP32x2 arithmetic) fused step for D3Q19.  Each entry: storage type, brick
-// bx x by, TMA pipeline depth.  These come before the scalar shapes of
-// lb_k1_d3q19.cu when the planner picks a default for a storage type.
+// bx x by, TMA pipeline depth.  Alternatives: the planner prefers the scalar
+// shapes of lb_k1_d3q19.cu for D3Q19, which measure faster.
 #include "lb_k2.cuh"
 
 namespace lbgb {

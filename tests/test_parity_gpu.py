@@ -89,8 +89,9 @@ def test_fused_equals_two_pass_bitwise(Solver, lat, storage, fname):
     assert np.array_equal(outs[1], outs[2])
 
 
-@pytest.mark.parametrize("lat,tile", [("D3Q19", (64, 7, 5)), ("D3Q27", (32, 10, 4))])
-@pytest.mark.parametrize("storage", ["f32", "f16s"])
+@pytest.mark.parametrize("lat,tile,storage", [("D3Q19", (64, 7, 5), "f32"), ("D3Q19", (64, 7, 5), "f16s"),
+                                              ("D3Q19", (64, 6, 5), "f32"), ("D3Q27", (32, 10, 4), "f32"),
+                                              ("D3Q27", (32, 10, 4), "f16s")])
 @pytest.mark.parametrize("fname", ["lid", "periodic", "duct"])
 def test_decoupled_export_warps_bitwise(Solver, lat, tile, storage, fname):
     """Brick shapes with dedicated export warps (decoupled from the node
