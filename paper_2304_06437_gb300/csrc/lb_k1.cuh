@@ -90,7 +90,7 @@ LB_HD constexpr int dir_of_sub(int axis, int sign, int ia) {
   return -1;
 }
 
-template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW>
+template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, int TS = 0>
 struct K1Shape {
   static constexpr int Q = L::Q;
   static constexpr int NTM = BX * BY;        // threads that own a node
@@ -126,7 +126,10 @@ struct K1Shape {
   static constexpr size_t OFF_STAGE = OFF_WIN + WB * align128(WIN);
   static constexpr size_t OFF_DESC = OFF_STAGE + align128(SR * STAGE);
   static constexpr size_t OFF_BAR = OFF_DESC + align128(size_t(PMAX) * 24);
-  static constexpr size_t SMEM = OFF_BAR + align128((NS + 2 * SR) * sizeof(uint64_t));
+  // TS: the completed plane leaves through a shared-memory output buffer and
+  // one TMA store instead of per-thread global stores
+  static constexpr size_t OFF_OUT = OFF_BAR + align128((NS + 2 * SR + 1) * sizeof(uint64_t));
+  static constexpr size_t SMEM = OFF_OUT + (TS ? align128(SLOT) : 0);
   static_assert(BY == 1 || NYF > 0, "a 2D brick has one internal row");
   static_assert(NXW > 0 || PMAX <= NTM, "perimeter larger than the CTA");
   static_assert(WB == 1 || WB == 2, "one or two window buffers");
@@ -268,10 +271,10 @@ __device__ __forceinline__ void export_lateral(const K1Args<R>& args, const R (&
 // Returns false if a TMA wait timed out (the CTA recorded LB_E_TIMEOUT and
 // must stop).  On return every copy the brick issued has completed and the
 // mbarriers are invalidated, so the CTA may start another brick.
-template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE>
+template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE, int TS = 0>
 __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args<R>& args, const int bI,
                                          const int bJ, const int bK) {
-  using Sh = K1Shape<L, S, R, BX, BY, NS, WB, NXW>;
+  using Sh = K1Shape<L, S, R, BX, BY, NS, WB, NXW, TS>;
   static_assert(WB == 2, "the pipelined sweep needs two window buffers");
   constexpr int Q = L::Q;
   constexpr int NTM = Sh::NTM;
@@ -334,8 +337,11 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   constexpr int SR = Sh::SR;
   uint64_t* sfull = bars + NS;        // staged plane ready (node threads arrive)
   uint64_t* sempty = bars + NS + SR;  // staged plane exported (export threads arrive)
+  uint64_t* outfree = bars + NS + 2 * SR;  // output buffer read by the last TMA store
+  S* outbuf = reinterpret_cast<S*>(smem + Sh::OFF_OUT);
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+    if constexpr (TS != 0) mbar_init(outfree, 1);
     if constexpr (DEC) {
       for (int s = 0; s < SR; ++s) {
         mbar_init(&sfull[s], NTM);
@@ -568,6 +574,7 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
 
   auto abort_cta = [&](int k) {
     if (tid == 0) {
+      if constexpr (TS != 0) bulk_wait_all();
       atomicExch(args.status, LB_E_TIMEOUT);
       // drain this CTA's own copies still in flight (bounded)
       for (int kk = (k < 0 ? 0 : k); kk < issued; ++kk) mbar_wait_bounded(&bars[kk % NS], (kk / NS) & 1, kWaitLimitNs);
@@ -677,13 +684,31 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
 
       // plane g - 1 is complete: store, stage its perimeter, export along z
       const int zd = g - 1;
+      if constexpr (TS != 0) {
+        // the output buffer is free once the TMA store of plane zd - 1 has read it
+        if (zd > z0 && zd < z1) {
+          if (tid == 0) {
+            bulk_wait_read_all();
+            mbar_arrive(outfree);
+          }
+          if (!mbar_wait_bounded(outfree, (zd - z0 - 1) & 1, kWaitLimitNs)) ok = false;
+        }
+      }
       if (active && zd >= z0 && zd < z1) {
-        S* p = fglob + (x + args.pitch * (y + int64_t(ny) * zd));
-        static_for<0, Q>([&](auto A_) {
-          constexpr int a = decltype(A_)::value;
-          *p = store_as<S, R>(G0[a]);
-          p += args.vol;
-        });
+        if constexpr (TS != 0) {
+          S* o = outbuf + ty * BX + tx;
+          static_for<0, Q>([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            o[a * BY * BX] = store_as<S, R>(G0[a]);
+          });
+        } else {
+          S* p = fglob + (x + args.pitch * (y + int64_t(ny) * zd));
+          static_for<0, Q>([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            *p = store_as<S, R>(G0[a]);
+            p += args.vol;
+          });
+        }
         if (pidx >= 0 && any_lateral_export) {
           const int sslot = DEC ? (zd - z0) % SR : (zd & 1);
           // the export warps must be done with this ring slot's previous plane
@@ -703,6 +728,9 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
       }
       // every node thread (staging or not) marks the staged plane ready
       if (DEC && zd >= z0 && zd < z1) mbar_arrive(&sfull[(zd - z0) % SR]);
+
+      // the output buffer's generic-proxy writes must be visible to the TMA
+      if (TS != 0 && zd >= z0 && zd < z1) fence_proxy_async_smem();
 
       // ring values move up one plane; start the loads two planes ahead
   #pragma unroll
@@ -725,6 +753,11 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
         abort_cta(c - z0);
         return false;
       }
+      // plane zd is complete in the output buffer: one TMA store writes it
+      if (TS != 0 && tid == 0 && zd >= z0 && zd < z1) {
+        tma_store_4d(tmap_p, x0, y0, zd, 0, outbuf);
+        bulk_commit();
+      }
       // refill the slot consumed by plane c with plane c + NS
       if (tid == 0 && c >= z0 && c < z1 && c + NS < z1) {
         const int slot = (c - z0) % NS;
@@ -739,21 +772,24 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   }
   // every issued plane has been waited for: retire the barriers so that the
   // next brick of a persistent CTA can initialise them again
+  if (TS != 0 && tid == 0) bulk_wait_all();  // the last plane's store has landed
   __syncthreads();
-  if (tid == 0)
+  if (tid == 0) {
     for (int s = 0; s < NS + (DEC ? 2 * SR : 0); ++s) mbar_inval(&bars[s]);
+    if constexpr (TS != 0) mbar_inval(outfree);
+  }
   __syncthreads();
   return true;
 #undef LB_RING_PUT
 }
 
 // One launch per time step of one domain: one CTA per brick column.
-template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE>
+template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE, int TS = 0>
 __global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
     k1_fused_step(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ K1Args<R> args) {
   const int nbx = args.nbx, nby = args.nby;
   const int b = blockIdx.x;
-  k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE>(&tmap, args, b % nbx, (b / nbx) % nby, b / (nbx * nby));
+  k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE, TS>(&tmap, args, b % nbx, (b / nbx) % nby, b / (nbx * nby));
 }
 
 // One launch per time step of many domains (a batch): a persistent grid whose
@@ -761,7 +797,7 @@ __global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
 // (domain, bI, bJ, bK); the arguments of domain d at shell parity p are
 // args[p * n_dom + d], and domain d's parity at this launch is
 // (dom_par[d] + k) & 1.
-template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE>
+template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE, int TS = 0>
 __global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
     k1_batched_step(const K1Args<R>* __restrict__ args, int n_dom, const CUtensorMap* __restrict__ tmaps,
                     const int4* __restrict__ items, const int* __restrict__ starts, const int* __restrict__ dom_par,
@@ -770,8 +806,8 @@ __global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
   for (int i = starts[blockIdx.x]; i < i1; ++i) {
     const int4 it = items[i];
     const int p = (dom_par[it.x] + k) & 1;
-    if (!k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE>(tmaps + it.x, args[size_t(p) * n_dom + it.x], it.y, it.z,
-                                                       it.w))
+    if (!k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE, TS>(tmaps + it.x, args[size_t(p) * n_dom + it.x], it.y,
+                                                           it.z, it.w))
       return;
   }
 }

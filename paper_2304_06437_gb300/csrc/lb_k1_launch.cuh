@@ -32,6 +32,7 @@ struct K1Variant {
   // number of its CTAs that fit on one SM
   cudaError_t (*batched)(const BatchLaunch&, cudaStream_t);
   int (*batched_occupancy)();
+  int ts;  // 1: completed planes leave through a TMA store (scalar kernel only)
 };
 
 // the compiled shape a fused-scheme context runs (lb_k1_plan.cu)
@@ -67,15 +68,15 @@ K1Args<R> k1_make_args(lb_ctx* ctx, int cur_parity, int next_parity) {
   return a;
 }
 
-template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW>
+template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, int TS = 0>
 struct K1Impl {
-  using Sh = K1Shape<L, S, R, BX, BY, NS, WB, NXW>;
+  using Sh = K1Shape<L, S, R, BX, BY, NS, WB, NXW, TS>;
 
   static cudaError_t configure() {
-    cudaError_t e = cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false>,
+    cudaError_t e = cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false, TS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::SMEM));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true>,
+    return cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true, TS>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::SMEM));
   }
 
@@ -84,9 +85,9 @@ struct K1Impl {
     make_bounce_terms<L, R>(ctx->g, a.bb);
     const int grid = ctx->plan.nbx * ctx->plan.nby * ctx->plan.nbz;
     if (ctx->g.has_force)
-      k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true><<<grid, Sh::NT, Sh::SMEM, ctx->stream>>>(ctx->tmap, a);
+      k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true, TS><<<grid, Sh::NT, Sh::SMEM, ctx->stream>>>(ctx->tmap, a);
     else
-      k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false><<<grid, Sh::NT, Sh::SMEM, ctx->stream>>>(ctx->tmap, a);
+      k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false, TS><<<grid, Sh::NT, Sh::SMEM, ctx->stream>>>(ctx->tmap, a);
     return cudaGetLastError();
   }
 
@@ -106,10 +107,10 @@ struct K1Impl {
   static cudaError_t batched(const BatchLaunch& b, cudaStream_t stream) {
     const K1Args<R>* args = static_cast<const K1Args<R>*>(b.args);
     if (b.force)
-      k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true><<<b.grid, Sh::NT, Sh::SMEM, stream>>>(
+      k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true, TS><<<b.grid, Sh::NT, Sh::SMEM, stream>>>(
           args, b.n_dom, b.tmaps, b.items, b.starts, b.dom_par, b.k);
     else
-      k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, false><<<b.grid, Sh::NT, Sh::SMEM, stream>>>(
+      k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, false, TS><<<b.grid, Sh::NT, Sh::SMEM, stream>>>(
           args, b.n_dom, b.tmaps, b.items, b.starts, b.dom_par, b.k);
     return cudaGetLastError();
   }
@@ -117,13 +118,13 @@ struct K1Impl {
   static int batched_occupancy() {
     const int sm = int(Sh::SMEM);
     if (configure() != cudaSuccess) return 0;
-    if (cudaFuncSetAttribute(k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, false>,
+    if (cudaFuncSetAttribute(k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, false, TS>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
-        cudaFuncSetAttribute(k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true>,
+        cudaFuncSetAttribute(k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true, TS>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
       return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true>, Sh::NT,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true, TS>, Sh::NT,
                                                       Sh::SMEM) != cudaSuccess)
       return 0;
     return n;
@@ -131,7 +132,7 @@ struct K1Impl {
 
   static constexpr K1Variant variant(int lattice, int storage) {
     return K1Variant{lattice, storage, BX, BY, NS, WB, NXW, Sh::SMEM, &configure, &step, &bootstrap, 1, &batched,
-                     &batched_occupancy};
+                     &batched_occupancy, TS};
   }
 };
 

@@ -223,3 +223,57 @@ def test_init_moments_device_buffers_and_readback(Solver):
     full = s.get_populations().reshape(19, 9, 17, 33)
     assert np.array_equal(box.reshape(19, 3, 2, 6), full[:, 5:8, 4:6, 3:9])
     s.close()
+
+
+@pytest.mark.parametrize("lat,storage", [("D3Q19", "f32"), ("D3Q27", "f16s"), ("D2Q9", "bf16s"), ("D3Q19", "f64")])
+def test_checkpoint_resume_is_bitwise(Solver, lat, storage):
+    """Checkpoint (lb_get_populations) and resume in a fresh context
+    (lb_set_populations, which rebuilds the brick shell) give exactly the
+    bits of an uninterrupted run for FP32 / FP16 / BF16 storage: the stored
+    shifted values round-trip exactly through f = ft + t_a rho0 in FP64, and
+    the shell is a function of the stored state.  FP64 storage loses the
+    last bits of ft in that sum, so there the resumed run agrees to rounding."""
+    dims = (70, 45, 1) if dim_of(lat) == 2 else (41, 19, 23)
+    faces, wall_u = faces_for(lat, "lid")
+    f0 = random_state(lat, dims, 61)
+    with Solver(lat, dims, 0.66, faces=faces, wall_u=wall_u, storage=storage) as s:
+        s.set_populations(np.ascontiguousarray(f0))
+        s.step(11)
+        want = s.get_populations()
+    with Solver(lat, dims, 0.66, faces=faces, wall_u=wall_u, storage=storage) as a:
+        a.set_populations(np.ascontiguousarray(f0))
+        a.step(4)
+        ckpt = a.get_populations()
+    with Solver(lat, dims, 0.66, faces=faces, wall_u=wall_u, storage=storage) as b:
+        b.set_populations(ckpt)
+        b.step(7)
+        got = b.get_populations()
+    if storage == "f64":
+        assert np.abs(got - want).max() < 1e-14
+    else:
+        assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("fname", ["lid", "periodic", "duct"])
+def test_tma_store_variant_bitwise(Solver, fname, monkeypatch):
+    """The brick shape whose completed planes leave through a shared-memory
+    buffer and one TMA store (64 x 8, two-slot ring) gives the two-pass bits,
+    including ragged bricks whose out-of-range lanes the store drops."""
+    lat, dims = "D3Q19", (150, 30, 23)
+    faces, wall_u = faces_for(lat, fname)
+    force = (2e-5, 0, 1e-5) if fname == "duct" else (0, 0, 0)
+    f0 = random_state(lat, dims, 78)
+    outs = []
+    for scheme, t in (("two_pass", None), ("fused", (64, 8, 5)), ("fused", (64, 8, 0))):
+        if scheme == "fused":
+            monkeypatch.setenv("LB_FUSED_PIPELINE", "2,0,-1,0")
+        s = Solver(lat, dims, 0.58, faces=faces, wall_u=wall_u, storage="f32", scheme=scheme, force=force, tile=t)
+        monkeypatch.delenv("LB_FUSED_PIPELINE", raising=False)
+        if scheme == "fused":
+            assert s.info()["tma_slots"] == 2 and s.info()["tile"][:2] == (64, 8)
+        s.set_populations(np.ascontiguousarray(f0))
+        s.step(9)
+        outs.append(s.get_populations())
+        s.close()
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
