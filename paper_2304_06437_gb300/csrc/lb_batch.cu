@@ -180,8 +180,8 @@ int setup_class(lb_batch& b, lb_batch::Class& c) {
   return LB_OK;
 }
 
-// Re-plan a member for batched throughput: the first compiled shape (in the
-// planner's order) whose bricks pad the cross-section by at most 25 %, else
+// Re-plan a member for batched throughput: the first plain compiled shape (in
+// the planner's order) whose bricks pad the cross-section by at most 25 %, else
 // the least padded one; and, for sweeps of up to 256 planes, one brick per
 // column, so that small domains do not pay the pipeline fill (slots + 2
 // planes) and the z-shell of short bricks.  Bits are unchanged.
@@ -193,7 +193,9 @@ int batch_replan(lb_ctx* x) {
   double least_waste = 1e300;
   for (int i = 0; i < nv; ++i) {
     const K1Variant* v = static_cast<const K1Variant*>(vs[i]);
-    if (!v->batched) continue;
+    // plain shapes only: the decoupled-export and TMA-store alternatives
+    // measure slower on the large domains they were tried on
+    if (!v->batched || v->nxw != 0 || v->ts != 0) continue;
     const double px = double((x->g.nx + v->bx - 1) / v->bx) * v->bx;
     const double py = double((x->g.ny + v->by - 1) / v->by) * v->by;
     const double waste = px * py / (double(x->g.nx) * double(x->g.ny));

@@ -10,6 +10,8 @@ namespace lbgb {
 extern const K1Variant k1_variants_d3q27[] = {
     K1Impl<D3Q27, float, float, 32,12,2,2,0>::variant(LB_D3Q27, LB_F32),
     K1Impl<D3Q27, float, float, 32,10,2,2,2>::variant(LB_D3Q27, LB_F32),  // + 2 decoupled export warps
+    K1Impl<D3Q27, float, float, 32,10,3,2,0>::variant(LB_D3Q27, LB_F32),  // deeper TMA ring
+    K1Impl<D3Q27, float, float, 32,8,3,2,0>::variant(LB_D3Q27, LB_F32),
     K1Impl<D3Q27, double, double, 32,4,2,2,0>::variant(LB_D3Q27, LB_F64),
     K1Impl<D3Q27, __half, float, 32,12,3,2,0>::variant(LB_D3Q27, LB_F16S),
     K1Impl<D3Q27, __half, float, 32,10,3,2,2>::variant(LB_D3Q27, LB_F16S),
