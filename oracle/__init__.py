@@ -12,6 +12,9 @@ Two implementations live here:
 * ``brute.py`` -- an independent numpy brute force for tiny grids that reaches
   the regularized set by a numerical weighted least-squares projection instead
   of the closed form, used to cross-check the C oracle.
+* ``lbm_oracle.c`` also holds the two-component colour-gradient step
+  (section 2.1: relaxation + perturbation of the total set, recolouring of
+  each colour), written in the paper's order with its readings stated there.
 * ``storage.py`` -- round-to-nearest-even of the shifted populations to the
   reduced storage formats (FP16, BF16), from the formats' definitions; with
   ``run_stored`` below it gives the exact reference of a reduced-precision run
@@ -54,6 +57,19 @@ class OrcCfg(ctypes.Structure):
     ]
 
 
+class OrcCgCfg(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int),
+        ("nx", ctypes.c_int),
+        ("ny", ctypes.c_int),
+        ("nz", ctypes.c_int),
+        ("tau", ctypes.c_double),
+        ("rho0", ctypes.c_double),
+        ("sigma", ctypes.c_double),
+        ("beta", ctypes.c_double),
+    ]
+
+
 def build(force: bool = False) -> str:
     """Compile the C oracle with gcc (-O2, OpenMP) into oracle/_build."""
     os.makedirs(_BUILD, exist_ok=True)
@@ -87,6 +103,11 @@ def lib():
             L.orc_run.argtypes = [P(OrcCfg), dp, ctypes.c_long, ctypes.c_int]
             L.orc_moments.argtypes = [P(OrcCfg), dp, dp, dp]
             L.orc_max_threads.argtypes = []
+            L.orc_cg_weights.argtypes = [ctypes.c_int, dp]
+            L.orc_cg_gradient.argtypes = [P(OrcCgCfg), dp, dp]
+            L.orc_cg_init.argtypes = [P(OrcCgCfg), dp, dp, dp, dp, dp]
+            L.orc_cg_run.argtypes = [P(OrcCgCfg), dp, dp, ctypes.c_long, ctypes.c_int]
+            L.orc_cg_fields.argtypes = [P(OrcCgCfg), dp, dp, dp, dp, dp]
             _lib = L
     return _lib
 
@@ -208,6 +229,69 @@ def run_stored(cfg: OrcCfg, f: np.ndarray, steps: int, storage: str, threads: in
     for _ in range(int(steps)):
         out = round_populations(run(cfg, out, 1, threads), w, storage, cfg.rho0)
     return out
+
+
+# ------------------------------------------------------------ colour gradient
+def make_cg_cfg(lattice, dims, tau, sigma, beta, rho0=1.0) -> OrcCgCfg:
+    """Two-component colour-gradient configuration (periodic box)."""
+    if isinstance(lattice, str):
+        lattice = LATTICE_NAMES[lattice]
+    c = OrcCgCfg()
+    c.lattice = lattice
+    nx, ny, nz = (list(dims) + [1, 1])[:3]
+    c.nx, c.ny, c.nz = int(nx), int(ny), int(nz)
+    c.tau, c.rho0, c.sigma, c.beta = float(tau), float(rho0), float(sigma), float(beta)
+    return c
+
+
+def cg_weights(lattice) -> np.ndarray:
+    if isinstance(lattice, str):
+        lattice = LATTICE_NAMES[lattice]
+    B = np.zeros(27)
+    q = lib().orc_cg_weights(lattice, _dp(B))
+    if q < 0:
+        raise ValueError("no colour-gradient weights for this lattice")
+    return B[:q]
+
+
+def cg_gradient(cfg: OrcCgCfg, phi: np.ndarray) -> np.ndarray:
+    N = cfg.nx * cfg.ny * cfg.nz
+    d = lib().orc_dim(cfg.lattice)
+    phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(N)
+    g = np.zeros((d, N))
+    assert lib().orc_cg_gradient(ctypes.byref(cfg), _dp(phi), _dp(g)) == 0
+    return g
+
+
+def cg_init(cfg: OrcCgCfg, rho_r, rho_b, u=None):
+    q = lib().orc_q(cfg.lattice)
+    N = cfg.nx * cfg.ny * cfg.nz
+    rr = np.ascontiguousarray(rho_r, dtype=np.float64).reshape(N)
+    rb = np.ascontiguousarray(rho_b, dtype=np.float64).reshape(N)
+    uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64).reshape(-1, N)
+    fr, fb = np.zeros((q, N)), np.zeros((q, N))
+    if lib().orc_cg_init(ctypes.byref(cfg), _dp(rr), _dp(rb), _dp(uu), _dp(fr), _dp(fb)) != 0:
+        raise ValueError("orc_cg_init rejected the configuration")
+    return fr, fb
+
+
+def cg_run(cfg: OrcCgCfg, fr, fb, steps: int, threads: int = 0):
+    """Advance copies of (f_R, f_B) by `steps`; returns the new pair."""
+    fr = np.ascontiguousarray(fr, dtype=np.float64).copy()
+    fb = np.ascontiguousarray(fb, dtype=np.float64).copy()
+    if lib().orc_cg_run(ctypes.byref(cfg), _dp(fr), _dp(fb), int(steps), int(threads)) != 0:
+        raise ValueError("orc_cg_run rejected the configuration")
+    return fr, fb
+
+
+def cg_fields(cfg: OrcCgCfg, fr, fb):
+    """(rho_R, rho_B, u) of a two-component state; u = sum (f_R + f_B) c / rho0."""
+    N = cfg.nx * cfg.ny * cfg.nz
+    d = lib().orc_dim(cfg.lattice)
+    rr, rb, u = np.zeros(N), np.zeros(N), np.zeros((d, N))
+    assert lib().orc_cg_fields(ctypes.byref(cfg), _dp(np.ascontiguousarray(fr)), _dp(np.ascontiguousarray(fb)),
+                               _dp(rr), _dp(rb), _dp(u)) == 0
+    return rr, rb, u
 
 
 def max_threads() -> int:

@@ -390,3 +390,204 @@ int orc_init(const orc_cfg* cfg, const double* rho, const double* u, const doubl
   }
   return 0;
 }
+
+/* ======================================================================== */
+/* Two-component colour-gradient model (paper section 2.1), periodic box.   */
+/* Per step, in the paper's order:                                          */
+/*  1. rho_R = sum f_R, rho_B = sum f_B, rho = rho_R + rho_B; the total     */
+/*     distribution g = f_R + f_B carries j = sum g c; u = j / rho0.        */
+/*  2. relaxation of g as in the single-component step (Eq. LBexp with the  */
+/*     Hermite-projected f^neq), plus the perturbation                       */
+/*       Omega1_a = (9/4) sigma omega |grad phi| [ t_a (c_a.grad phi)^2 /    */
+/*                  |grad phi|^2 - B_a ]                                     */
+/*     -- reading: the paper prints (c_a.grad phi) without the square, which */
+/*     would inject momentum; the squared form (the one of the cited CG     */
+/*     models) conserves mass and momentum when sum B = cs2 and sum B c c =  */
+/*     cs2 I.  phi = (rho_R - rho_B) / rho; grad phi by the isotropic        */
+/*     stencil (1/cs2) sum_a t_a c_a phi(x + c_a).                           */
+/*  3. recolouring (Latva-Kokko):                                            */
+/*       f_R* = (rho_R/rho) g* + beta (rho_R rho_B / rho) t_a cos(theta_a)   */
+/*       f_B* = (rho_B/rho) g* - beta (rho_R rho_B / rho) t_a cos(theta_a)   */
+/*     cos(theta_a) = c_a.grad phi / (|c_a| |grad phi|), 0 for the rest      */
+/*     vector or a vanishing gradient -- reading: the paper prints + for     */
+/*     both colours; the opposite signs keep f_R* + f_B* = g*, and the zero- */
+/*     velocity equilibrium is taken per unit density (t_a).                 */
+/*  4. each colour streams (pull, periodic wrap).                            */
+/* ======================================================================== */
+
+/* perturbation weights B_a by |c|^2 shell (they satisfy sum B = cs2 and
+ * sum B c_x^2 = cs2; the remaining freedom as in the D2Q9 / D3Q19 CG models
+ * the paper cites) */
+static double cg_B_of(int lattice, int c2) {
+  if (lattice == ORC_D2Q9) {
+    static const double b[3] = {-4.0 / 27.0, 2.0 / 27.0, 5.0 / 108.0};
+    return b[c2];
+  }
+  static const double b[3] = {-2.0 / 9.0, 1.0 / 54.0, 1.0 / 27.0};
+  return b[c2];
+}
+
+int orc_cg_weights(int lattice, double* B) {
+  lattice_t L;
+  if (lattice == ORC_D3Q27 || build_lattice(lattice, &L) < 0) return -1;
+  for (int a = 0; a < L.q; ++a)
+    B[a] = cg_B_of(lattice, L.c[a][0] * L.c[a][0] + L.c[a][1] * L.c[a][1] + L.c[a][2] * L.c[a][2]);
+  return L.q;
+}
+
+static int cg_check(const orc_cg_cfg* cfg, lattice_t* L) {
+  if (!cfg || cfg->lattice == ORC_D3Q27 || build_lattice(cfg->lattice, L) < 0) return -1;
+  if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || !(cfg->tau > 0.5) || !(cfg->rho0 > 0.0)) return -1;
+  if (L->d == 2 && cfg->nz != 1) return -1;
+  return 0;
+}
+
+static long cg_wrap(long v, long n) { v %= n; return v < 0 ? v + n : v; }
+
+int orc_cg_gradient(const orc_cg_cfg* cfg, const double* phi, double* grad) {
+  lattice_t L;
+  if (cg_check(cfg, &L) < 0 || !phi || !grad) return -1;
+  const long nx = cfg->nx, ny = cfg->ny, nz = cfg->nz, N = nx * ny * nz;
+#pragma omp parallel for schedule(static)
+  for (long idx = 0; idx < N; ++idx) {
+    const long x = idx % nx, y = (idx / nx) % ny, z = idx / (nx * ny);
+    double gsum[3] = {0, 0, 0};
+    for (int a = 0; a < L.q; ++a) {
+      const long xn = cg_wrap(x + L.c[a][0], nx), yn = cg_wrap(y + L.c[a][1], ny), zn = cg_wrap(z + L.c[a][2], nz);
+      const double p = phi[xn + nx * (yn + ny * zn)];
+      for (int al = 0; al < 3; ++al) gsum[al] += L.w[a] * L.c[a][al] * p;
+    }
+    for (int al = 0; al < L.d; ++al) grad[al * N + idx] = gsum[al] / CS2;
+  }
+  return 0;
+}
+
+int orc_cg_init(const orc_cg_cfg* cfg, const double* rho_r, const double* rho_b, const double* u, double* fr,
+                double* fb) {
+  lattice_t L;
+  if (cg_check(cfg, &L) < 0 || !rho_r || !rho_b || !fr || !fb) return -1;
+  const long N = (long)cfg->nx * cfg->ny * cfg->nz;
+#pragma omp parallel for schedule(static)
+  for (long idx = 0; idx < N; ++idx) {
+    double uu[3] = {0, 0, 0};
+    if (u)
+      for (int al = 0; al < L.d; ++al) uu[al] = u[al * N + idx];
+    const double rho = rho_r[idx] + rho_b[idx];
+    double feq[QMAX];
+    equilibrium(&L, cfg->rho0, rho, uu, feq);
+    for (int a = 0; a < L.q; ++a) {
+      fr[(long)a * N + idx] = rho_r[idx] / rho * feq[a];
+      fb[(long)a * N + idx] = rho_b[idx] / rho * feq[a];
+    }
+  }
+  return 0;
+}
+
+int orc_cg_fields(const orc_cg_cfg* cfg, const double* fr, const double* fb, double* rho_r, double* rho_b,
+                  double* u) {
+  lattice_t L;
+  if (cg_check(cfg, &L) < 0 || !fr || !fb) return -1;
+  const long N = (long)cfg->nx * cfg->ny * cfg->nz;
+#pragma omp parallel for schedule(static)
+  for (long idx = 0; idx < N; ++idx) {
+    double rr = 0.0, rb = 0.0, j[3] = {0, 0, 0};
+    for (int a = 0; a < L.q; ++a) {
+      const double r = fr[(long)a * N + idx], b = fb[(long)a * N + idx];
+      rr += r;
+      rb += b;
+      for (int al = 0; al < 3; ++al) j[al] += (r + b) * L.c[a][al];
+    }
+    if (rho_r) rho_r[idx] = rr;
+    if (rho_b) rho_b[idx] = rb;
+    if (u)
+      for (int al = 0; al < L.d; ++al) u[al * N + idx] = j[al] / cfg->rho0;
+  }
+  return 0;
+}
+
+int orc_cg_run(const orc_cg_cfg* cfg, double* fr, double* fb, long steps, int nthreads) {
+  lattice_t L;
+  if (cg_check(cfg, &L) < 0 || !fr || !fb || steps < 0) return -1;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+  const long nx = cfg->nx, ny = cfg->ny, nz = cfg->nz, N = nx * ny * nz;
+  const int q = L.q, d = L.d;
+  const double omega = 1.0 / cfg->tau;
+  double B[QMAX];
+  for (int a = 0; a < q; ++a)
+    B[a] = cg_B_of(cfg->lattice, L.c[a][0] * L.c[a][0] + L.c[a][1] * L.c[a][1] + L.c[a][2] * L.c[a][2]);
+  double* phi = (double*)malloc(sizeof(double) * N);
+  double* grad = (double*)malloc(sizeof(double) * 3 * N);
+  double* pr = (double*)malloc(sizeof(double) * q * N);
+  double* pb = (double*)malloc(sizeof(double) * q * N);
+  if (!phi || !grad || !pr || !pb) {
+    free(phi); free(grad); free(pr); free(pb);
+    return -2;
+  }
+  for (long t = 0; t < steps; ++t) {
+    /* phase field of the current state, then its gradient */
+#pragma omp parallel for schedule(static)
+    for (long idx = 0; idx < N; ++idx) {
+      double rr = 0.0, rb = 0.0;
+      for (int a = 0; a < q; ++a) {
+        rr += fr[(long)a * N + idx];
+        rb += fb[(long)a * N + idx];
+      }
+      phi[idx] = (rr - rb) / (rr + rb);
+    }
+    orc_cg_gradient(cfg, phi, grad);
+    /* collide: relax + perturb the total set, then recolour */
+#pragma omp parallel for schedule(static)
+    for (long idx = 0; idx < N; ++idx) {
+      double g[QMAX], gpc[QMAX];
+      double rr = 0.0, rb = 0.0;
+      for (int a = 0; a < q; ++a) {
+        const double r = fr[(long)a * N + idx], b = fb[(long)a * N + idx];
+        rr += r;
+        rb += b;
+        g[a] = r + b;
+      }
+      orc_cfg one = {cfg->lattice, 1, 1, 1, cfg->tau, cfg->rho0, {0, 0, 0}, {0, 0, 0, 0, 0, 0}, {{0}}};
+      collide(&L, &one, g, gpc, 0);
+      const double rho = rr + rb;
+      double gv[3] = {0, 0, 0}, g2 = 0.0;
+      for (int al = 0; al < d; ++al) {
+        gv[al] = grad[al * N + idx];
+        g2 += gv[al] * gv[al];
+      }
+      const double gn = sqrt(g2);
+      for (int a = 0; a < q; ++a) {
+        double cg = 0.0, c2 = 0.0;
+        for (int al = 0; al < d; ++al) {
+          cg += L.c[a][al] * gv[al];
+          c2 += L.c[a][al] * L.c[a][al];
+        }
+        double pert = 0.0, cosv = 0.0;
+        if (gn > 0.0) {
+          pert = 2.25 * cfg->sigma * omega * gn * (L.w[a] * cg * cg / g2 - B[a]);
+          if (c2 > 0.0) cosv = cg / (sqrt(c2) * gn);
+        }
+        const double gs = gpc[a] + pert;
+        const double rec = cfg->beta * rr * rb / rho * L.w[a] * cosv;
+        pr[(long)a * N + idx] = rr / rho * gs + rec;
+        pb[(long)a * N + idx] = rb / rho * gs - rec;
+      }
+    }
+    /* stream each colour: pull from x - c_a with periodic wrap */
+#pragma omp parallel for schedule(static)
+    for (long idx = 0; idx < N; ++idx) {
+      const long x = idx % nx, y = (idx / nx) % ny, z = idx / (nx * ny);
+      for (int a = 0; a < q; ++a) {
+        const long xs = cg_wrap(x - L.c[a][0], nx), ys = cg_wrap(y - L.c[a][1], ny), zs = cg_wrap(z - L.c[a][2], nz);
+        const long src = xs + nx * (ys + ny * zs);
+        fr[(long)a * N + idx] = pr[(long)a * N + src];
+        fb[(long)a * N + idx] = pb[(long)a * N + src];
+      }
+    }
+  }
+  free(phi); free(grad); free(pr); free(pb);
+  return 0;
+}

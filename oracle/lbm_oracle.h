@@ -75,6 +75,24 @@ int orc_run(const orc_cfg* cfg, double* f, long steps, int nthreads);
 /* Density and velocity of the stored state: rho = sum f, u = (j + F/2)/rho0. */
 int orc_moments(const orc_cfg* cfg, const double* f, double* rho, double* u);
 
+/* Two-component colour-gradient model (section 2.1), periodic box, D2Q9 or
+ * D3Q19.  The two colours are stored as f_R, f_B ([q][N] each); see
+ * lbm_oracle.c for the step and the readings it takes. */
+typedef struct {
+  int lattice;          /* ORC_D2Q9 / ORC_D3Q19 */
+  int nx, ny, nz;
+  double tau, rho0;
+  double sigma;         /* surface tension parameter of the perturbation */
+  double beta;          /* recolouring parameter (interface width) */
+} orc_cg_cfg;
+int orc_cg_weights(int lattice, double* B);  /* perturbation weights B_a; returns q */
+int orc_cg_gradient(const orc_cg_cfg* cfg, const double* phi, double* grad);  /* [d][N] */
+int orc_cg_init(const orc_cg_cfg* cfg, const double* rho_r, const double* rho_b, const double* u,
+                double* fr, double* fb);
+int orc_cg_run(const orc_cg_cfg* cfg, double* fr, double* fb, long steps, int nthreads);
+int orc_cg_fields(const orc_cg_cfg* cfg, const double* fr, const double* fb, double* rho_r, double* rho_b,
+                  double* u);
+
 /* Number of OpenMP threads a parallel region would use (0 without OpenMP). */
 int orc_max_threads(void);
 
