@@ -285,6 +285,41 @@ LB_API int lb_batch_info(const lb_batch* b, lb_batch_info_t* info);
 /* Frees the batch (not its contexts).  NULL is allowed. */
 LB_API void lb_batch_destroy(lb_batch* b);
 
+/* --------------------------------------------------- two-component model
+ * The paper's colour-gradient (CG) model for two immiscible fluids, red and
+ * blue (section 2.1), in the thread-safe form of section 4: per step one
+ * launch takes the moments of each node (the regularized relaxation
+ * coefficients of the total set g = f_R + f_B, the concentrations and the
+ * phase field phi = (rho_R - rho_B)/rho), one takes grad phi by the isotropic
+ * stencil (1/cs2) sum_a t_a c_a phi(x + c_a), and one rebuilds both colours
+ * at every node from the upstream node's fields:
+ *   g*_a = [Eq. LBexp with fhat^neq]_a + (9/4) sigma omega |grad phi|
+ *          [t_a (c_a.n)^2 - B_a]                          (perturbation)
+ *   f_R,a = (rho_R/rho) g*_a + beta (rho_R rho_B/rho) t_a (c_a.n)/|c_a|,
+ *   f_B,a = g*_a - f_R,a                                  (recolouring)
+ * with n = grad phi / |grad phi| and B_a = -4/27, 2/27, 5/108 (D2Q9) or
+ * -2/9, 1/54, 1/27 (D3Q19) by |c|^2 shell.  Each colour is one population
+ * array.  Periodic box, D2Q9 or D3Q19, LB_F64 or LB_F32 (storage and
+ * arithmetic); rho0 = 1; u = sum_a (f_R + f_B) c_a / rho0.
+ * Arrays are FP64 in the conventions above ([q][N] populations, [d][N]
+ * velocity); host (on_device = 0) or device (1) pointers.
+ * lb_cg_create: tau > 1/2, sigma >= 0 (surface tension), 0 <= beta <= 1
+ *   (interface width); starts as an even mixture at rest.  stream as for
+ *   lb_options.stream.  Errors: LB_E_INVAL, LB_E_UNSUPPORTED (other lattice
+ *   or storage), LB_E_NOMEM, LB_E_CUDA.
+ * lb_cg_init: f_k = (rho_k/rho) f^eq(rho, u) (Eq. equil); u may be NULL.
+ * lb_cg_step enqueues n steps; the others synchronise the stream. */
+typedef struct lb_cg lb_cg;
+LB_API int lb_cg_create(int32_t lattice, const int64_t dims[3], double tau, double sigma, double beta,
+                        int32_t storage, void* stream, lb_cg** out);
+LB_API int lb_cg_init(lb_cg* c, const double* rho_r, const double* rho_b, const double* u, int32_t on_device);
+LB_API int lb_cg_set_populations(lb_cg* c, const double* f_r, const double* f_b, int32_t on_device);
+LB_API int lb_cg_get_populations(lb_cg* c, double* f_r, double* f_b, int32_t on_device);
+LB_API int lb_cg_step(lb_cg* c, int64_t n);
+LB_API int lb_cg_fields(lb_cg* c, double* rho_r, double* rho_b, double* u, int32_t on_device);
+LB_API int lb_cg_sync(lb_cg* c);
+LB_API void lb_cg_destroy(lb_cg* c);
+
 /* Self-test of the bounded wait that every kernel applies to its mbarrier
  * waits (the paper has no counterpart: failure detection of this library).
  * Launches one tiny kernel that waits on a barrier nothing completes, for at

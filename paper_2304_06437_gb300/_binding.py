@@ -140,6 +140,15 @@ SIGNATURES = {
     "lb_batch_sync": (ctypes.c_int, [_vp]),
     "lb_batch_info": (ctypes.c_int, [_vp, _P(lb_batch_info_t)]),
     "lb_batch_destroy": (None, [_vp]),
+    "lb_cg_create": (ctypes.c_int, [ctypes.c_int32, _i64p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_int32, _vp, _P(_vp)]),
+    "lb_cg_init": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32]),
+    "lb_cg_set_populations": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32]),
+    "lb_cg_get_populations": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32]),
+    "lb_cg_step": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "lb_cg_fields": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32]),
+    "lb_cg_sync": (ctypes.c_int, [_vp]),
+    "lb_cg_destroy": (None, [_vp]),
     "lb_selftest_timeout": (ctypes.c_int, [ctypes.c_int64, _i64p]),
     "lb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lb_abi_version": (ctypes.c_int, []),

@@ -231,6 +231,82 @@ class Batch:
         self.close()
 
 
+class CGSolver:
+    """Two-component colour-gradient domain (lb_cg_*): periodic box, D2Q9 or
+    D3Q19, storage "f64" or "f32"."""
+
+    def __init__(self, lattice, dims, tau, sigma, beta, storage="f32", stream=None):
+        self._lib = B.load()
+        self.lat_id = B.LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+        self.d = 2 if self.lat_id == B.LB_D2Q9 else 3
+        self.q = 9 if self.lat_id == B.LB_D2Q9 else 19
+        dims = list(dims) + [1] * (3 - len(dims))
+        self.dims = tuple(int(v) for v in dims[:3])
+        self.n = self.dims[0] * self.dims[1] * self.dims[2]
+        self._c = ctypes.c_void_p()
+        st = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream))) if stream is not None else None
+        B.check(self._lib.lb_cg_create(self.lat_id, (ctypes.c_int64 * 3)(*self.dims), float(tau), float(sigma),
+                                       float(beta), B.STORAGES[storage] if isinstance(storage, str) else int(storage),
+                                       st, ctypes.byref(self._c)), "lb_cg_create")
+
+    def init(self, rho_r, rho_b, u=None):
+        pr, dev = _ptr(rho_r)
+        pb, dev2 = _ptr(rho_b)
+        pu, dev3 = _ptr(u)
+        if u is None:
+            dev3 = dev
+        if not (dev == dev2 == dev3):
+            raise ValueError("rho_r, rho_b and u must all be host or all be device buffers")
+        B.check(self._lib.lb_cg_init(self._c, pr, pb, pu, dev), "lb_cg_init")
+
+    def set_populations(self, fr, fb):
+        pr, dev = _ptr(fr)
+        pb, dev2 = _ptr(fb)
+        if dev != dev2:
+            raise ValueError("f_r and f_b must both be host or both be device buffers")
+        B.check(self._lib.lb_cg_set_populations(self._c, pr, pb, dev), "lb_cg_set_populations")
+
+    def get_populations(self):
+        fr, fb = np.empty((self.q, self.n)), np.empty((self.q, self.n))
+        B.check(self._lib.lb_cg_get_populations(self._c, ctypes.c_void_p(fr.ctypes.data),
+                                                ctypes.c_void_p(fb.ctypes.data), 0), "lb_cg_get_populations")
+        return fr, fb
+
+    def step(self, n=1):
+        B.check(self._lib.lb_cg_step(self._c, int(n)), "lb_cg_step")
+
+    def sync(self):
+        B.check(self._lib.lb_cg_sync(self._c), "lb_cg_sync")
+
+    def fields(self, rho_r=None, rho_b=None, u=None):
+        """(rho_R, rho_B, u); pass torch CUDA tensors to stay on the device."""
+        if rho_r is None and rho_b is None and u is None:
+            rho_r, rho_b, u = np.empty(self.n), np.empty(self.n), np.empty((self.d, self.n))
+        ptrs = [_ptr(x) for x in (rho_r, rho_b, u)]
+        devs = {d for (p, d), x in zip(ptrs, (rho_r, rho_b, u)) if x is not None}
+        if len(devs) != 1:
+            raise ValueError("outputs must all be host or all be device buffers")
+        B.check(self._lib.lb_cg_fields(self._c, ptrs[0][0], ptrs[1][0], ptrs[2][0], devs.pop()), "lb_cg_fields")
+        return rho_r, rho_b, u
+
+    def close(self):
+        if getattr(self, "_c", None) and self._c.value:
+            self._lib.lb_cg_destroy(self._c)
+            self._c = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 def lattice_table(lattice):
     lib = B.load()
     lid = B.LATTICES[lattice] if isinstance(lattice, str) else int(lattice)

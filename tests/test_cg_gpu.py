@@ -1,0 +1,99 @@
+"""The two-component colour-gradient step on the GPU (lb_cg_*) against the
+FP64 oracle of the same step (oracle.cg_*), through the C ABI.
+
+FP64: populations within 1e-13 after one step, fields within 1e-12 relative
+L2 after twenty; FP32: 1e-5.  A static droplet run on the GPU gives the
+oracle's pressure jump (Laplace's law is pinned on the oracle).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from lbcase import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lb():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2304_06437_gb300 import build
+    build.build()
+    import paper_2304_06437_gb300 as P
+    return P
+
+
+def _droplet_state(dims, seed):
+    d = 2 if dims[2] == 1 else 3
+    nx, ny, nz = dims
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    r = np.sqrt((x - nx / 2.3) ** 2 + (y - ny / 1.9) ** 2 + ((z - nz / 2.1) ** 2 if d == 3 else 0)).ravel()
+    phi = np.tanh((min(nx, ny) / 3.0 - r) / 2.0)
+    _, u, _ = synth.smooth_random_state(dims, d, seed=seed, du=0.02)
+    return (1 + phi) / 2, (1 - phi) / 2, np.ascontiguousarray(u)
+
+
+CASES = [("D2Q9", (37, 29, 1)), ("D3Q19", (13, 11, 9))]
+
+
+@pytest.mark.parametrize("lat,dims", CASES)
+@pytest.mark.parametrize("storage,ftol,tol", [("f64", 1e-13, 1e-12), ("f32", 2e-6, 1e-5)])
+def test_cg_matches_oracle(lb, lat, dims, storage, ftol, tol):
+    tau, sigma, beta = 0.8, 0.02, 0.7
+    rr, rb, u = _droplet_state(dims, 3)
+    cfg = oracle.make_cg_cfg(lat, dims, tau, sigma, beta)
+    fr0, fb0 = oracle.cg_init(cfg, rr, rb, u)
+    with lb.CGSolver(lat, dims, tau, sigma, beta, storage=storage) as s:
+        s.set_populations(np.ascontiguousarray(fr0), np.ascontiguousarray(fb0))
+        s.step(1)
+        gr, gb = s.get_populations()
+        rr1, rb1 = oracle.cg_run(cfg, fr0, fb0, 1)
+        assert np.abs(gr - rr1).max() < ftol and np.abs(gb - rb1).max() < ftol
+        s.step(19)
+        R, Bc, uu = s.fields()
+    fr20, fb20 = oracle.cg_run(cfg, fr0, fb0, 20)
+    R0, B0, u0 = oracle.cg_fields(cfg, fr20, fb20)
+    assert rel_l2(R, R0) < tol and rel_l2(Bc, B0) < tol
+    assert rel_l2(uu, u0) < tol * 10, rel_l2(uu, u0)
+
+
+def test_cg_init_matches_oracle_init(lb):
+    lat, dims = "D3Q19", (12, 10, 8)
+    rr, rb, u = _droplet_state(dims, 8)
+    cfg = oracle.make_cg_cfg(lat, dims, 0.7, 0.01, 0.5)
+    fr0, fb0 = oracle.cg_init(cfg, rr, rb, u)
+    with lb.CGSolver(lat, dims, 0.7, 0.01, 0.5, storage="f64") as s:
+        s.init(rr, rb, u)
+        gr, gb = s.get_populations()
+        R, Bc, uu = s.fields()
+    assert np.abs(gr - fr0).max() < 1e-15 and np.abs(gb - fb0).max() < 1e-15
+    assert np.abs(R - rr).max() < 1e-14 and np.abs(uu - u).max() < 1e-14
+
+
+def test_cg_static_droplet_pressure_jump(lb):
+    """2D droplet (R = 12, sigma = 0.01) after 3000 steps: the GPU's pressure
+    jump equals the oracle's, which obeys Laplace's law (CPU pin)."""
+    n, R, sigma = 64, 12, 0.01
+    x, y = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    r = np.sqrt((x - (n - 1) / 2) ** 2 + (y - (n - 1) / 2) ** 2).ravel()
+    phi = np.tanh((R - r) / 2.0)
+    rr, rb = (1 + phi) / 2, (1 - phi) / 2
+    cfg = oracle.make_cg_cfg("D2Q9", (n, n), 1.0, sigma, 0.7)
+    fr, fb = oracle.cg_run(cfg, *oracle.cg_init(cfg, rr, rb), 3000)
+    Ro, Bo, _ = oracle.cg_fields(cfg, fr, fb)
+
+    def jump(rho):
+        rho = rho.reshape(n, n)
+        c = n // 2
+        return (rho[c - 2:c + 2, c - 2:c + 2].mean() - rho[:4, :4].mean()) / 3.0
+
+    for storage, tol in (("f64", 1e-9), ("f32", 2e-3)):
+        with lb.CGSolver("D2Q9", (n, n), 1.0, sigma, 0.7, storage=storage) as s:
+            s.init(rr, rb)
+            s.step(3000)
+            R_, B_, _ = s.fields()
+        dp_gpu, dp_ora = jump(R_ + B_), jump(Ro + Bo)
+        assert abs(dp_gpu - dp_ora) < tol * abs(dp_ora), (storage, dp_gpu, dp_ora)
+        assert abs(dp_gpu * R / sigma - 1) < 0.05
