@@ -114,6 +114,50 @@ LB_HD constexpr int pair_first(int p) {
 // off-diagonal slot of an axis pair (0,1)->0, (0,2)->1, (1,2)->2
 LB_HD constexpr int od(int al, int be) { return al + be - 1; }
 
+// pairs whose velocity has a nonzero component along axis al, and the k-th
+template <class L>
+LB_HD constexpr int axis_pair_count(int al) {
+  int n = 0;
+  for (int p = 0; p < n_pairs<L>(); ++p) n += comp<L>(al, pair_first<L>(p)) != 0 ? 1 : 0;
+  return n;
+}
+template <class L>
+LB_HD constexpr int axis_pair(int al, int k) {
+  for (int p = 0; p < n_pairs<L>(); ++p)
+    if (comp<L>(al, pair_first<L>(p)) != 0) {
+      if (k == 0) return p;
+      --k;
+    }
+  return -1;
+}
+// pairs with nonzero components along both al and be, and the k-th
+template <class L>
+LB_HD constexpr int od_pair_count(int al, int be) {
+  int n = 0;
+  for (int p = 0; p < n_pairs<L>(); ++p) n += comp<L>(al, pair_first<L>(p)) * comp<L>(be, pair_first<L>(p)) != 0;
+  return n;
+}
+template <class L>
+LB_HD constexpr int od_pair(int al, int be, int k) {
+  for (int p = 0; p < n_pairs<L>(); ++p)
+    if (comp<L>(al, pair_first<L>(p)) * comp<L>(be, pair_first<L>(p)) != 0) {
+      if (k == 0) return p;
+      --k;
+    }
+  return -1;
+}
+
+// balanced pairwise sum of term(k), k in [Lo, Hi)
+template <int Lo, int Hi, class R, class F>
+LB_DEV R tree_sum(F&& term) {
+  if constexpr (Hi - Lo == 1) {
+    return term(std::integral_constant<int, Lo>{});
+  } else {
+    constexpr int Mid = Lo + (Hi - Lo) / 2;
+    return tree_sum<Lo, Mid, R>(term) + tree_sum<Mid, Hi, R>(term);
+  }
+}
+
 // ------------------------------------------------------------ moments
 template <class L, class R, bool FORCE>
 LB_DEV void moments(const R (&f)[L::Q], const Phys<R>& ph, Mom<R>& m) {
@@ -126,28 +170,39 @@ LB_DEV void moments(const R (&f)[L::Q], const Phys<R>& ph, Mom<R>& m) {
     s[p] = f[a] + f[b];
     t[p] = f[a] - f[b];
   });
-  R drho = f[0];
-  static_for<0, n_pairs<L>()>([&](auto P) { drho = drho + s[decltype(P)::value]; });
+  // the sums run as balanced trees (short dependency chains for the FMA
+  // pipe); every kernel evaluates this same order, so the schedules agree
+  // bit for bit
+  constexpr int NP = n_pairs<L>();
+  const R drho = tree_sum<0, NP + 1, R>([&](auto K) -> R {
+    constexpr int k = decltype(K)::value;
+    if constexpr (k == 0) return f[0];
+    else return s[k - 1];
+  });
   R j[3] = {R(0), R(0), R(0)};
   R Pd[3] = {R(0), R(0), R(0)};
   R Po[3] = {R(0), R(0), R(0)};
-  static_for<0, n_pairs<L>()>([&](auto P) {
-    constexpr int p = decltype(P)::value;
-    static_for<0, 3>([&](auto AL) {
-      constexpr int al = decltype(AL)::value;
-      constexpr int ca = comp<L>(al, pair_first<L>(p));
-      if constexpr (ca == 1) j[al] = j[al] + t[p];
-      if constexpr (ca == -1) j[al] = j[al] - t[p];
-      if constexpr (ca != 0) Pd[al] = Pd[al] + s[p];
-    });
-    static_for<0, 3>([&](auto AL) {
-      constexpr int al = decltype(AL)::value;
-      static_for<al + 1, 3>([&](auto BE) {
-        constexpr int be = decltype(BE)::value;
-        constexpr int cc = comp<L>(al, pair_first<L>(p)) * comp<L>(be, pair_first<L>(p));
-        if constexpr (cc == 1) Po[od(al, be)] = Po[od(al, be)] + s[p];
-        if constexpr (cc == -1) Po[od(al, be)] = Po[od(al, be)] - s[p];
+  static_for<0, 3>([&](auto AL) {
+    constexpr int al = decltype(AL)::value;
+    constexpr int n = axis_pair_count<L>(al);
+    if constexpr (n > 0) {
+      j[al] = tree_sum<0, n, R>([&](auto K) -> R {
+        constexpr int p = axis_pair<L>(al, decltype(K)::value);
+        if constexpr (comp<L>(al, pair_first<L>(p)) == 1) return t[p];
+        else return -t[p];
       });
+      Pd[al] = tree_sum<0, n, R>([&](auto K) -> R { return s[axis_pair<L>(al, decltype(K)::value)]; });
+    }
+    static_for<al + 1, 3>([&](auto BE) {
+      constexpr int be = decltype(BE)::value;
+      constexpr int no = od_pair_count<L>(al, be);
+      if constexpr (no > 0) {
+        Po[od(al, be)] = tree_sum<0, no, R>([&](auto K) -> R {
+          constexpr int p = od_pair<L>(al, be, decltype(K)::value);
+          if constexpr (comp<L>(al, pair_first<L>(p)) * comp<L>(be, pair_first<L>(p)) == 1) return s[p];
+          else return -s[p];
+        });
+      }
     });
   });
   m.drho = drho;
