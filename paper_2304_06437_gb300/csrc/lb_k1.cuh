@@ -108,8 +108,14 @@ struct K1Shape {
   static constexpr int H = 2 * HW + 2 * HS;
   static constexpr int HPT = (H + NTM - 1) / NTM;
   static constexpr int PMAX = NYF > 0 ? 2 * BX + 2 * (BY - 2) : 2;  // lateral perimeter nodes
+  // lateral export entries, one per (perimeter node, face): segments W, E,
+  // S, N, each starting on a warp boundary in 3D so that every export warp
+  // writes a single face (a corner node has an entry in two segments)
+  static constexpr int SEGY = NYF > 0 ? (BY + 31) / 32 * 32 : 1;
+  static constexpr int SEGX = NYF > 0 ? (BX + 31) / 32 * 32 : 0;
+  static constexpr int PE = 2 * SEGY + 2 * SEGX;
   // export warps: the first NEXW node-owning warps, or NXW dedicated ones
-  static constexpr int NEXW = NXW > 0 ? NXW : (PMAX + 31) / 32;
+  static constexpr int NEXW = NXW > 0 ? NXW : (PE + 31) / 32;
   // stage row of one perimeter node: Q values padded so that the row is a
   // whole, odd number of 16-byte units (vector stores, conflict-free loads)
   static constexpr int VEC = 16 / int(sizeof(R));
@@ -125,13 +131,13 @@ struct K1Shape {
   static constexpr int SR = DEC ? 4 : 2;
   static constexpr size_t OFF_STAGE = OFF_WIN + WB * align128(WIN);
   static constexpr size_t OFF_DESC = OFF_STAGE + align128(SR * STAGE);
-  static constexpr size_t OFF_BAR = OFF_DESC + align128(size_t(PMAX) * 24);
+  static constexpr size_t OFF_BAR = OFF_DESC + align128(size_t(PE) * 12);
   // TS: the completed plane leaves through a shared-memory output buffer and
   // one TMA store instead of per-thread global stores
   static constexpr size_t OFF_OUT = OFF_BAR + align128((NS + 2 * SR + 1) * sizeof(uint64_t));
   static constexpr size_t SMEM = OFF_OUT + (TS ? align128(SLOT) : 0);
   static_assert(BY == 1 || NYF > 0, "a 2D brick has one internal row");
-  static_assert(NXW > 0 || PMAX <= NTM, "perimeter larger than the CTA");
+  static_assert(NXW > 0 || 32 * NEXW <= NTM, "export entries need more warps than the CTA has");
   static_assert(WB == 1 || WB == 2, "one or two window buffers");
 };
 
@@ -266,6 +272,42 @@ __device__ __forceinline__ void export_lateral(const K1Args<R>& args, const R (&
   }
 }
 
+// Export entry e of a brick shape: its face (0 W, 1 E, 2 S, 3 N) and the
+// first entry of that face's segment.
+template <class Sh>
+__device__ __forceinline__ int export_face_of(int e) {
+  if (e < Sh::SEGY) return 0;
+  if (e < 2 * Sh::SEGY) return 1;
+  return e < 2 * Sh::SEGY + Sh::SEGX ? 2 : 3;
+}
+template <class Sh>
+__device__ __forceinline__ int export_seg_start(int face) {
+  return face < 2 ? face * Sh::SEGY : 2 * Sh::SEGY + (face - 2) * Sh::SEGX;
+}
+
+// Collide the completed (rounded) state of a lateral perimeter node once more
+// and export the populations that leave through one face; dst is the node's
+// record of that face in this plane, stride the distance between directions.
+template <class L, class S, class R, bool FORCE>
+__device__ __forceinline__ void export_one_face(const K1Args<R>& args, const R (&fin)[L::Q], int face, R* dst,
+                                                int64_t stride) {
+  R fr[L::Q];
+  static_for<0, L::Q>([&](auto A_) {
+    constexpr int a = decltype(A_)::value;
+    fr[a] = round_to_storage<S, R>(fin[a]);
+  });
+  Mom<R> m;
+  moments<L, R, FORCE>(fr, args.ph, m);
+  Coef<R> kc;
+  coeffs<L, R, FORCE>(m, args.ph, kc);
+  if (face == 0) export_face<L, R, 0, -1>(kc, {dst, stride});
+  else if (face == 1) export_face<L, R, 0, 1>(kc, {dst, stride});
+  if constexpr (count_dirs<L>(1, 1) > 0) {
+    if (face == 2) export_face<L, R, 1, -1>(kc, {dst, stride});
+    else if (face == 3) export_face<L, R, 1, 1>(kc, {dst, stride});
+  }
+}
+
 // The sweep of one brick column (bI, bJ, bK) of one domain by the whole CTA.
 // tmap_p is the domain's TMA descriptor (kernel-parameter or global memory).
 // Returns false if a TMA wait timed out (the CTA recorded LB_E_TIMEOUT and
@@ -281,7 +323,7 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   constexpr int NXF = Sh::NXF, NYF = Sh::NYF, NZF = Sh::NZF;
   constexpr int PY = Sh::PY, WX = Sh::WX, WPLANE = Sh::WPLANE;
   constexpr int HW = Sh::HW, HS = Sh::HS, H = Sh::H, HPT = Sh::HPT;
-  constexpr int PMAX = Sh::PMAX, NEXW = Sh::NEXW, QP = Sh::QP, VEC = Sh::VEC;
+  constexpr int PMAX = Sh::PMAX, NEXW = Sh::NEXW, QP = Sh::QP, VEC = Sh::VEC, PE = Sh::PE;
   constexpr int WY = Sh::WY;
   constexpr int WSTRIDE = int(align128(Sh::WIN) / sizeof(R));  // between window buffers
   using Vec = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
@@ -291,10 +333,10 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   R* win0 = reinterpret_cast<R*>(smem + Sh::OFF_WIN);
   R* stage = reinterpret_cast<R*>(smem + Sh::OFF_STAGE);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Sh::OFF_BAR);
-  // per perimeter node: shell offsets (plane 0) of its x-face and y-face
-  // records, and its face flags
+  // per export entry: shell offset (plane 0) of the face record, and the
+  // stage row of the node (-1: no neighbour across that face)
   int64_t* desc_off = reinterpret_cast<int64_t*>(smem + Sh::OFF_DESC);
-  unsigned* desc_faces = reinterpret_cast<unsigned*>(smem + Sh::OFF_DESC + size_t(PMAX) * 16);
+  int* desc_p = reinterpret_cast<int*>(smem + Sh::OFF_DESC + size_t(PE) * 8);
 
   const int tid = threadIdx.x;
   const bool is_main = tid < NTM;  // owns node (tx, ty); the rest only export
@@ -450,13 +492,12 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
 
   // perimeter (lateral boundary) slot of this node, and export-warp work
   const int pidx = active ? perimeter_index<NYF>(tx, ty, bxa, bya) : -1;
-  const int pcount = perimeter_count<NYF>(bxa, bya);
   const bool any_lateral_export = nbW || nbE || (NYF > 0 && (nbS || nbN));
   // shared export warps start at warp EXW0: past the first brick row, whose
   // warps also stage a whole row of perimeter nodes every plane
   constexpr int EXW0 = (NXW == 0 && NTM / 32 >= NEXW + 4 && BY >= 4) ? 2 : 0;
   const bool exp_warp = any_lateral_export && (NXW > 0 ? !is_main : (warp >= EXW0 && warp < EXW0 + NEXW));
-  const int exp_lane = NXW > 0 ? tid - NTM : (warp - EXW0) * 32 + lane;  // first perimeter node of this lane
+  const int exp_lane = NXW > 0 ? tid - NTM : (warp - EXW0) * 32 + lane;  // first export entry of this lane
 
   // this thread's own cell in the window (interior of the padding ring)
   const int wbase = (ty + PY) * WX + (tx + 1);
@@ -466,17 +507,19 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   const int64_t nzy = int64_t(nz) * ny, nzx = int64_t(nz) * nx;
   if (exp_warp) {
 #pragma unroll 1
-    for (int p = exp_lane; p < pcount; p += 32 * Sh::NEXW) {
-      int ptx, pty;
-      perimeter_node<NYF>(p, bxa, bya, ptx, pty);
-      const unsigned faces = (ptx == 0 && nbW ? kFaceW : 0u) | (ptx == bxa - 1 && nbE ? kFaceE : 0u) |
-                             (NYF > 0 && pty == 0 && nbS ? kFaceS : 0u) |
-                             (NYF > 0 && pty == bya - 1 && nbN ? kFaceN : 0u);
-      // SX[side][I][ia][z][y], SY[side][J][ia][z][x]; side 0 here, side 1 is
-      // a brick-uniform distance further (a node may export through both)
-      desc_off[2 * p] = args.sx_off + (int64_t(bI) * NXF) * nzy + (y0 + pty);
-      desc_off[2 * p + 1] = NYF > 0 ? args.sy_off + (int64_t(bJ) * NYF) * nzx + (x0 + ptx) : 0;
-      desc_faces[p] = faces;
+    for (int e = exp_lane; e < PE; e += 32 * Sh::NEXW) {
+      const int face = export_face_of<Sh>(e);
+      const int k = e - export_seg_start<Sh>(face);  // position along the face
+      const bool xface = face < 2;
+      const int ptx = xface ? (face == 0 ? 0 : bxa - 1) : k;
+      const int pty = xface ? k : (face == 2 ? 0 : bya - 1);
+      const bool nb = face == 0 ? nbW : (face == 1 ? nbE : (face == 2 ? nbS : nbN));
+      const bool ok = nb && (xface ? pty < bya : ptx < bxa) && k < (xface ? Sh::SEGY : Sh::SEGX);
+      // SX[side][I][ia][z][y], SY[side][J][ia][z][x]; the high face (E, N)
+      // is the side-1 record, a brick-uniform distance further
+      desc_off[e] = xface ? args.sx_off + ((int64_t(face == 1 ? nbx : 0) + bI) * NXF) * nzy + (y0 + pty)
+                          : args.sy_off + ((int64_t(face == 3 ? nby : 0) + bJ) * NYF) * nzx + (x0 + ptx);
+      desc_p[e] = ok ? perimeter_index<NYF>(ptx, pty, bxa, bya) : -1;
     }
   }
   // (the first barrier of the sweep orders these writes before their use)
@@ -485,7 +528,9 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
     if (exp_warp && zx >= z0 && zx < z1) {
       R* shn = args.sh_next;
 #pragma unroll 1
-      for (int p = exp_lane; p < pcount; p += 32 * Sh::NEXW) {
+      for (int e = exp_lane; e < PE; e += 32 * Sh::NEXW) {
+        const int p = desc_p[e];
+        if (p < 0) continue;
         const Vec* st = reinterpret_cast<const Vec*>(stage + sslot * (QP * PMAX) + p * QP);
         R fin[QP];
 #pragma unroll
@@ -493,9 +538,10 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
         R fq[Q];
 #pragma unroll
         for (int a = 0; a < Q; ++a) fq[a] = fin[a];
-        export_lateral<L, S, R, FORCE>(args, fq, desc_faces[p], shn + desc_off[2 * p] + int64_t(zx) * ny,
-                                       shn + desc_off[2 * p + 1] + int64_t(zx) * nx, int64_t(nbx) * NXF * nzy,
-                                       int64_t(nby) * NYF * nzx, nzy, nzx);
+        const int face = export_face_of<Sh>(e);
+        const bool xface = face < 2;
+        export_one_face<L, S, R, FORCE>(args, fq, face, shn + desc_off[e] + int64_t(zx) * (xface ? ny : nx),
+                                        xface ? nzy : nzx);
       }
     }
   };
@@ -618,6 +664,10 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
       const bool real_g = g >= z0 && g < z1;
       const bool need_g = plane_needed(g);
 
+      // exports of plane g - 2 (staged one iteration ago) first: they need
+      // no TMA data, so they overlap the wait for plane c's load
+      if constexpr (!DEC) export_staged(g - 2, (g - 2) & 1);
+
       R onl_c[3] = {R(0), R(0), R(0)};
       bool ok = true;
       if (c <= z1) {
@@ -638,9 +688,6 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
           if constexpr (cz == 1) G2[a] = v;
         });
       }
-      // exports of plane g - 2 (staged one iteration ago)
-      if constexpr (!DEC) export_staged(g - 2, (g - 2) & 1);
-
       // z-descending bounce-backs of plane g - 1, saved one plane ago
       if (bdn_mask) {
         static_for<0, Q>([&](auto A_) {
