@@ -90,6 +90,21 @@ LB_HD constexpr int dir_of_sub(int axis, int sign, int ia) {
   return -1;
 }
 
+// lateral window slot of the ia-th direction whose component along axis is
+// sign, for a run-time ia: a chain of compile-time candidates, so that no
+// lattice table is laid out in local memory
+template <class L, int axis, int sign>
+__device__ __forceinline__ int lat_slot_of_sub(int ia) {
+  int r = 0;
+  static_for<0, L::Q>([&](auto A_) {
+    constexpr int a = decltype(A_)::value;
+    if constexpr (comp<L>(axis, a) == sign) {
+      if (ia == sub_index<L>(axis, sign, a)) r = lat_index<L>(a);
+    }
+  });
+  return r;
+}
+
 template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, int TS = 0>
 struct K1Shape {
   static constexpr int Q = L::Q;
@@ -246,29 +261,6 @@ __device__ __forceinline__ void export_node(const K1Args<R>& args, const R (&fin
       export_face<L, R, 2, -1>(kc, {shn + args.sz_off + (int64_t(bK) * NZF) * nyx + row, nyx});
     if (faces & kFaceU)
       export_face<L, R, 2, 1>(kc, {shn + args.sz_off + ((int64_t(args.nbz) + bK) * NZF) * nyx + row, nyx});
-  }
-}
-
-// Export of one lateral perimeter node whose shell locations were resolved
-// once per brick: pw / ps point at the node's low-side x-face / y-face record
-// of this plane; the high-side records lie dxe / dyn elements further.
-template <class L, class S, class R, bool FORCE>
-__device__ __forceinline__ void export_lateral(const K1Args<R>& args, const R (&fin)[L::Q], unsigned faces, R* pw,
-                                               R* ps, int64_t dxe, int64_t dyn, int64_t sxs, int64_t sys) {
-  R fr[L::Q];
-  static_for<0, L::Q>([&](auto A_) {
-    constexpr int a = decltype(A_)::value;
-    fr[a] = round_to_storage<S, R>(fin[a]);
-  });
-  Mom<R> m;
-  moments<L, R, FORCE>(fr, args.ph, m);
-  Coef<R> kc;
-  coeffs<L, R, FORCE>(m, args.ph, kc);
-  if (faces & kFaceW) export_face<L, R, 0, -1>(kc, {pw, sxs});
-  if (faces & kFaceE) export_face<L, R, 0, 1>(kc, {pw + dxe, sxs});
-  if constexpr (count_dirs<L>(1, 1) > 0) {
-    if (faces & kFaceS) export_face<L, R, 1, -1>(kc, {ps, sys});
-    if (faces & kFaceN) export_face<L, R, 1, 1>(kc, {ps + dyn, sys});
   }
 }
 
@@ -438,7 +430,6 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
           if (args.per[1]) sy = (sy + ny) % ny;
           else ok = false;
         }
-        const int a = dir_of_sub<L>(0, west ? 1 : -1, ia);
         const int col = west ? 0 : bxa + 1;
         // the west ring holds the high-face export (side 1) of the west brick
         const int side = west ? 1 : 0;
@@ -446,7 +437,7 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
         hval[e] = ok;
         hbase[e] = args.sx_off + ((int64_t(side) * nbx + bb) * NXF + ia) * int64_t(nz) * ny + sy;
         hzs[e] = ny;
-        hsm[e] = lat_index<L>(a) * WPLANE + r * WX + col;
+        hsm[e] = (west ? lat_slot_of_sub<L, 0, 1>(ia) : lat_slot_of_sub<L, 0, -1>(ia)) * WPLANE + r * WX + col;
       } else {
         const int h2 = h - 2 * HW;
         const bool south = h2 < HS;
@@ -454,14 +445,13 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
         const int ia = hh / BX;
         const int i = hh % BX;
         const bool ok = (south ? nbS : nbN) && i < bxa;
-        const int a = dir_of_sub<L>(1, south ? 1 : -1, ia);
         const int row = south ? 0 : bya + 1;
         const int side = south ? 1 : 0;
         const int bb = south ? bJs : bJn;
         hval[e] = ok;
         hbase[e] = args.sy_off + ((int64_t(side) * nby + bb) * NYF + ia) * int64_t(nz) * nx + x0 + i;
         hzs[e] = nx;
-        hsm[e] = lat_index<L>(a) * WPLANE + row * WX + 1 + i;
+        hsm[e] = (south ? lat_slot_of_sub<L, 1, 1>(ia) : lat_slot_of_sub<L, 1, -1>(ia)) * WPLANE + row * WX + 1 + i;
       }
     }
   }
@@ -524,6 +514,7 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   }
   // (the first barrier of the sweep orders these writes before their use)
 
+  constexpr bool kLateExport = std::is_same<S, __nv_bfloat16>::value;
   auto export_staged = [&](int zx, int sslot) {
     if (exp_warp && zx >= z0 && zx < z1) {
       R* shn = args.sh_next;
@@ -665,8 +656,10 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
       const bool need_g = plane_needed(g);
 
       // exports of plane g - 2 (staged one iteration ago) first: they need
-      // no TMA data, so they overlap the wait for plane c's load
-      if constexpr (!DEC) export_staged(g - 2, (g - 2) & 1);
+      // no TMA data, so they overlap the wait for plane c's load (BF16
+      // storage keeps them after the gather: its rounding needs registers
+      // that the earlier placement would spill)
+      if constexpr (!DEC && !kLateExport) export_staged(g - 2, (g - 2) & 1);
 
       R onl_c[3] = {R(0), R(0), R(0)};
       bool ok = true;
@@ -688,6 +681,8 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
           if constexpr (cz == 1) G2[a] = v;
         });
       }
+      if constexpr (!DEC && kLateExport) export_staged(g - 2, (g - 2) & 1);
+
       // z-descending bounce-backs of plane g - 1, saved one plane ago
       if (bdn_mask) {
         static_for<0, Q>([&](auto A_) {
