@@ -79,17 +79,6 @@ LB_HD constexpr int lat_index(int a) {
   for (int b = 0; b < a; ++b) n += is_lateral<L>(b) ? 1 : 0;
   return n;
 }
-// the ia-th direction whose component along axis is sign
-template <class L>
-LB_HD constexpr int dir_of_sub(int axis, int sign, int ia) {
-  for (int a = 0; a < L::Q; ++a)
-    if (comp<L>(axis, a) == sign) {
-      if (ia == 0) return a;
-      --ia;
-    }
-  return -1;
-}
-
 // lateral window slot of the ia-th direction whose component along axis is
 // sign, for a run-time ia: a chain of compile-time candidates, so that no
 // lattice table is laid out in local memory

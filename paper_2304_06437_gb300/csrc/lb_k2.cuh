@@ -230,14 +230,13 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
           if (args.per[1]) sy = (sy + ny) % ny;
           else ok = false;
         }
-        const int a = dir_of_sub<L>(0, west ? 1 : -1, ia);
         const int col = west ? 0 : bxa + 1;
         const int side = west ? 1 : 0;
         const int bb = west ? bIw : bIe;
         hval[e] = ok;
         hbase[e] = args.sx_off + ((int64_t(side) * nbx + bb) * NXF + ia) * int64_t(nz) * ny + sy;
         hzs[e] = ny;
-        hsm[e] = lat_index<L>(a) * WPLANE + r * WX + col;
+        hsm[e] = (west ? lat_slot_of_sub<L, 0, 1>(ia) : lat_slot_of_sub<L, 0, -1>(ia)) * WPLANE + r * WX + col;
       } else {
         const int h2 = h - 2 * HW;
         const bool south = h2 < HS;
@@ -245,14 +244,13 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
         const int ia = hh / BX;
         const int i = hh % BX;
         const bool ok = (south ? nbS : nbN) && i < bxa;
-        const int a = dir_of_sub<L>(1, south ? 1 : -1, ia);
         const int row = south ? 0 : bya + 1;
         const int side = south ? 1 : 0;
         const int bb = south ? bJs : bJn;
         hval[e] = ok;
         hbase[e] = args.sy_off + ((int64_t(side) * nby + bb) * NYF + ia) * int64_t(nz) * nx + x0 + i;
         hzs[e] = nx;
-        hsm[e] = lat_index<L>(a) * WPLANE + row * WX + 1 + i;
+        hsm[e] = (south ? lat_slot_of_sub<L, 1, 1>(ia) : lat_slot_of_sub<L, 1, -1>(ia)) * WPLANE + row * WX + 1 + i;
       }
     }
   }
