@@ -38,6 +38,8 @@ WORKLOADS = {
     "cavity_d3q19_1024": dict(lattice="D3Q19", dims=(1024, 1024, 1024), tau=0.52, flow="cavity", lid=0.05),
     "cavity_d3q19_512": dict(lattice="D3Q19", dims=(512, 512, 512), tau=0.52, flow="cavity", lid=0.05),
     "cavity_d3q19_256": dict(lattice="D3Q19", dims=(256, 256, 256), tau=0.52, flow="cavity", lid=0.05),
+    # profiling case: 2.5 GB, yet every brick sweeps 512 planes as at 1024^3
+    "cavity_d3q19_256x512": dict(lattice="D3Q19", dims=(256, 256, 512), tau=0.52, flow="cavity", lid=0.05),
     "tg_d3q27_512": dict(lattice="D3Q27", dims=(512, 512, 512), tau=0.8, flow="tg3d", u0=0.02),
     "tg_d3q27_256": dict(lattice="D3Q27", dims=(256, 256, 256), tau=0.8, flow="tg3d", u0=0.02),
     "tg_d2q9_16384": dict(lattice="D2Q9", dims=(16384, 16384, 1), tau=0.8, flow="tg2d", u0=0.01),

@@ -271,10 +271,12 @@ LB_DEV void coeffs(const Mom<R>& m, const Phys<R>& ph, Coef<R>& k) {
 
 // ------------------------------------------------------------ one population
 // ft*_a = t_a (even + odd), even = A + sum_{c_al != 0} C_alal + sum c_al c_be C2,
-// odd = sum c_al B_al; evaluated as fma(t_a, even, t_a odd)
+// odd = sum c_al B_al; evaluated as fma(t_a, even, t_a odd).  post_parts
+// returns even and t_a odd; opp(a) has the same even part and exactly the
+// negated odd part (every term of its sum is negated)
 template <class L, class R, int a>
-LB_DEV R post(const Coef<R>& k) {
-  R even = k.A;
+LB_DEV void post_parts(const Coef<R>& k, R& even, R& wodd) {
+  even = k.A;
   static_for<0, 3>([&](auto AL) {
     constexpr int al = decltype(AL)::value;
     if constexpr (comp<L>(al, a) != 0) even = even + k.C[al];
@@ -288,8 +290,7 @@ LB_DEV R post(const Coef<R>& k) {
       if constexpr (cc == -1) even = even - k.C2[od(al, be)];
     });
   });
-  // odd part: the sum of the signed B components in axis order; for opp(a)
-  // every term is negated, so the result is exactly negated as well
+  // odd part: the sum of the signed B components in axis order
   R odd = R(0);
   bool first = true;
   static_for<0, 3>([&](auto AL) {
@@ -301,21 +302,37 @@ LB_DEV R post(const Coef<R>& k) {
       first = false;
     }
   });
-  constexpr R w = R(weight<L>(a));
-  if (first) return w * even;  // rest population: no odd part
-  return fma_r(w, even, w * odd);
+  wodd = R(weight<L>(a)) * odd;
 }
 
-// full regularized collision of one node: ft -> ft*
+template <class L, class R, int a>
+LB_DEV R post(const Coef<R>& k) {
+  constexpr R w = R(weight<L>(a));
+  R even, wodd;
+  post_parts<L, R, a>(k, even, wodd);
+  if constexpr (a == 0) return w * even;  // rest population: no odd part
+  else return fma_r(w, even, wodd);
+}
+
+// full regularized collision of one node: ft -> ft*; the two members of a
+// velocity pair share the even part and take -/+ the odd part
 template <class L, class R, bool FORCE>
 LB_DEV void collide(const R (&f)[L::Q], const Phys<R>& ph, R (&out)[L::Q]) {
   Mom<R> m;
   moments<L, R, FORCE>(f, ph, m);
   Coef<R> k;
   coeffs<L, R, FORCE>(m, ph, k);
-  static_for<0, L::Q>([&](auto A_) {
-    constexpr int a = decltype(A_)::value;
-    out[a] = post<L, R, a>(k);
+  static_assert(L::cx(0) == 0 && L::cy(0) == 0 && L::cz(0) == 0, "direction 0 is the rest population");
+  out[0] = post<L, R, 0>(k);
+  static_for<0, n_pairs<L>()>([&](auto P) {
+    constexpr int p = decltype(P)::value;
+    constexpr int a = pair_first<L>(p);
+    constexpr int b = L::opp(a);
+    constexpr R w = R(weight<L>(a));
+    R even, wodd;
+    post_parts<L, R, a>(k, even, wodd);
+    out[a] = fma_r(w, even, wodd);
+    out[b] = fma_r(w, even, -wodd);
   });
 }
 

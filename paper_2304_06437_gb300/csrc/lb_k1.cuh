@@ -320,7 +320,9 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   int* desc_p = reinterpret_cast<int*>(smem + Sh::OFF_DESC + size_t(PE) * 8);
 
   const int tid = threadIdx.x;
-  const bool is_main = tid < NTM;  // owns node (tx, ty); the rest only export
+  // owns node (tx, ty); the rest only export (all threads without dedicated
+  // export warps: the launch has exactly NTM threads then)
+  const bool is_main = NXW == 0 || tid < NTM;
   const int tx = tid % BX;
   const int ty = is_main ? tid / BX : BY;
   const int warp = tid / 32, lane = tid % 32;

@@ -96,8 +96,8 @@ def test_fused_equals_two_pass_bitwise(Solver, lat, storage, fname):
 def test_decoupled_export_warps_bitwise(Solver, lat, tile, storage, fname):
     """Brick shapes with dedicated export warps (decoupled from the node
     warps' per-plane barrier through the staged-plane ring) give the same
-    bits as the paper's two-pass schedule, on grids spanning many bricks
-    and ring laps (sweeps of 4-5 planes, 13-23 planes per column)."""
+    bits as the paper's two-pass schedule, on grids spanning many (ragged)
+    bricks and ring laps (sweeps of 4-5 planes, 13-23 planes per column)."""
     dims = (150, 30, 23) if lat == "D3Q19" else (70, 33, 13)
     faces, wall_u = faces_for(lat, fname)
     force = (2e-5, 0, 1e-5) if fname == "duct" else (0, 0, 0)
