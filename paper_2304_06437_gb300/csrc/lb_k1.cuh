@@ -140,6 +140,12 @@ struct K1Shape {
   // one TMA store instead of per-thread global stores
   static constexpr size_t OFF_OUT = OFF_BAR + align128((NS + 2 * SR + 1) * sizeof(uint64_t));
   static constexpr size_t SMEM = OFF_OUT + (TS ? align128(SLOT) : 0);
+  // the plane sweep runs three planes per loop trip (the three gathered
+  // sets change roles at compile time instead of being copied every plane)
+  // where the three copies of the body still fit the registers: up to 19
+  // FP32 arithmetic values per node, and not with BF16 storage, whose
+  // rounding takes the registers that the unrolled body would need
+  static constexpr bool UNROLL3 = Q * sizeof(R) <= 76 && !std::is_same<S, __nv_bfloat16>::value;
   static_assert(BY == 1 || NYF > 0, "a 2D brick has one internal row");
   static_assert(NXW > 0 || 32 * NEXW <= NTM, "export entries need more warps than the CTA has");
   static_assert(WB == 1 || WB == 2, "one or two window buffers");
@@ -585,12 +591,15 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   }
 
   // three destination planes of gathered populations
-  R G0[Q], G1[Q], G2[Q];  // planes g-1, g, g+1 of the plane g being gathered
+  // (the sweep below runs three planes per loop trip and permutes the roles
+  // of the three sets at compile time instead of copying them every plane;
+  // an entry is always gathered, or set by a bounce-back, before it is stored)
+  R G[3][Q];
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
-    G0[a] = R(0);
-    G1[a] = R(0);
-    G2[a] = R(0);
+    G[0][a] = R(0);
+    G[1][a] = R(0);
+    G[2][a] = R(0);
   }
   // bounce-back values of the z-descending directions of the previous plane;
   // applied after the next gather, which would otherwise overwrite them
@@ -639,7 +648,11 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
 
     // ------------------------------------------------ sweep: gather plane g,
     // produce plane g + 1 in the same barrier interval (independent work)
-    for (int g = z0 - 1; g <= z1; ++g) {
+    auto sweep_plane = [&](const int g, auto K) -> bool {
+      constexpr int k = decltype(K)::value;
+      R(&G0)[Q] = G[k % 3];        // plane g - 1
+      R(&G1)[Q] = G[(k + 1) % 3];  // plane g
+      R(&G2)[Q] = G[(k + 2) % 3];  // plane g + 1
       const int c = g + 1;
       R* win_g = win0 + (g & 1) * WSTRIDE;
       R* win_c = win0 + (c & 1) * WSTRIDE;
@@ -770,12 +783,6 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
       for (int e = 0; e < HPT; ++e) ha[e] = hb[e];
       halo_fetch(hb, c + 2);
 
-      // rotate: plane g's partial set becomes the "previous" plane
-  #pragma unroll
-      for (int a = 0; a < Q; ++a) {
-        G0[a] = G1[a];
-        G1[a] = G2[a];
-      }
       onl_g[0] = onl_c[0];
       onl_g[1] = onl_c[1];
       onl_g[2] = onl_c[2];
@@ -798,10 +805,27 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
         tma_load_4d(slots + size_t(slot) * Q * BY * BX, tmap_p, x0, y0, c + NS, 0, &bars[slot]);
         ++issued;
       }
+      return true;
+    };
+    // planes z0 - 1 .. z1 + 1 (the last trips only export the staged top
+    // plane and pass the barrier; every thread runs the same trips)
+    if constexpr (Sh::UNROLL3) {
+      for (int g = z0 - 1; g <= z1 + 1; g += 3) {
+        if (!sweep_plane(g, std::integral_constant<int, 0>{})) return false;
+        if (!sweep_plane(g + 1, std::integral_constant<int, 1>{})) return false;
+        if (!sweep_plane(g + 2, std::integral_constant<int, 2>{})) return false;
+      }
+    } else {
+      for (int g = z0 - 1; g <= z1 + 1; ++g) {
+        if (!sweep_plane(g, std::integral_constant<int, 0>{})) return false;
+        // plane g's partial set becomes the previous plane's
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+          G[0][a] = G[1][a];
+          G[1][a] = G[2][a];
+        }
+      }
     }
-
-    // exports of the last two planes
-    if constexpr (!DEC) export_staged(z1 - 1, (z1 - 1) & 1);
   }
   // every issued plane has been waited for: retire the barriers so that the
   // next brick of a persistent CTA can initialise them again
