@@ -143,9 +143,11 @@ struct K1Shape {
   // the plane sweep runs three planes per loop trip (the three gathered
   // sets change roles at compile time instead of being copied every plane)
   // where the three copies of the body still fit the registers: up to 19
-  // FP32 arithmetic values per node, and not with BF16 storage, whose
-  // rounding takes the registers that the unrolled body would need
-  static constexpr bool UNROLL3 = Q * sizeof(R) <= 76 && !std::is_same<S, __nv_bfloat16>::value;
+  // FP32 arithmetic values per node, or 27 in a CTA of at most 256 threads,
+  // and not with BF16 storage, whose rounding takes the registers that the
+  // unrolled body would need
+  static constexpr bool UNROLL3 = (Q * sizeof(R) <= 76 || (Q * sizeof(R) <= 108 && NT <= 256)) &&
+                                  !std::is_same<S, __nv_bfloat16>::value;
   static_assert(BY == 1 || NYF > 0, "a 2D brick has one internal row");
   static_assert(NXW > 0 || 32 * NEXW <= NTM, "export entries need more warps than the CTA has");
   static_assert(WB == 1 || WB == 2, "one or two window buffers");
