@@ -105,7 +105,7 @@ __device__ __forceinline__ void export_lateral_pair(const K1Args<float>& args, c
 // Returns false if a TMA wait timed out (the CTA recorded LB_E_TIMEOUT and
 // must stop).  On return every copy the brick issued has completed and the
 // mbarriers are invalidated, so the CTA may start another brick.
-template <class L, class S, int BX, int BY, int NS, bool FORCE>
+template <class L, class S, int BX, int BY, int NS, bool FORCE, bool UNROLL3 = false>
 __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args<float>& args, const int bI,
                                          const int bJ, const int bK) {
   using R = float;
@@ -393,12 +393,15 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
       if (hval[e]) (win_)[hsm[e]] = ha[e];             \
   }
 
-  V G0[Q], G1[Q], G2[Q];
+  // three destination planes of gathered pairs; with UNROLL3 the sweep
+  // permutes their roles at compile time (three copies of its body),
+  // otherwise it copies them every plane
+  V G[3][Q];
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
-    G0[a] = V(0);
-    G1[a] = V(0);
-    G2[a] = V(0);
+    G[0][a] = V(0);
+    G[1][a] = V(0);
+    G[2][a] = V(0);
   }
   constexpr int NDN = count_dirs<L>(2, -1);
   V bdn[NDN];
@@ -426,7 +429,11 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
   for (int e = 0; e < HPT; ++e) ha[e] = hb[e];
   halo_fetch(hb, z0 + 1);
 
-  for (int g = z0 - 1; g <= z1; ++g) {
+  auto sweep_plane = [&](const int g, auto K) -> bool {
+    constexpr int k = decltype(K)::value;
+    V(&G0)[Q] = G[k % 3];        // plane g - 1
+    V(&G1)[Q] = G[(k + 1) % 3];  // plane g
+    V(&G2)[Q] = G[(k + 2) % 3];  // plane g + 1
     const int c = g + 1;
     R* win_g = win0 + (g & 1) * WSTRIDE;
     R* win_c = win0 + (c & 1) * WSTRIDE;
@@ -582,11 +589,6 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
     for (int e = 0; e < HPT; ++e) ha[e] = hb[e];
     halo_fetch(hb, c + 2);
 
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
-      G0[a] = G1[a];
-      G1[a] = G2[a];
-    }
     onl_g[0] = onl_c[0];
     onl_g[1] = onl_c[1];
     onl_g[2] = onl_c[2];
@@ -601,9 +603,26 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
       tma_load_4d(slots + size_t(slot) * Q * BY * BX, tmap_p, x0, y0, c + NS, 0, &bars[slot]);
       ++issued;
     }
+    return true;
+  };
+  // planes z0 - 1 .. z1 + 1 (the last trips only export the staged top plane
+  // and pass the barrier; every thread runs the same trips)
+  if constexpr (UNROLL3) {
+    for (int g = z0 - 1; g <= z1 + 1; g += 3) {
+      if (!sweep_plane(g, std::integral_constant<int, 0>{})) return false;
+      if (!sweep_plane(g + 1, std::integral_constant<int, 1>{})) return false;
+      if (!sweep_plane(g + 2, std::integral_constant<int, 2>{})) return false;
+    }
+  } else {
+    for (int g = z0 - 1; g <= z1 + 1; ++g) {
+      if (!sweep_plane(g, std::integral_constant<int, 0>{})) return false;
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        G[0][a] = G[1][a];
+        G[1][a] = G[2][a];
+      }
+    }
   }
-
-  export_staged(z1 - 1);
   // every issued plane has been waited for: retire the barriers so that the
   // next brick of a persistent CTA can initialise them again
   __syncthreads();
@@ -616,11 +635,11 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
 
 // One launch per time step of one domain: one CTA per brick column.
 template <class L, class S, int BX, int BY, int NS, bool FORCE>
-__global__ void __launch_bounds__(BX* BY / 2, 1)
+__global__ void __launch_bounds__(BX* BY / 2, (L::Q == 9 ? 3 : 1))
     k2_fused_step(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ K1Args<float> args) {
   const int nbx = args.nbx, nby = args.nby;
   const int b = blockIdx.x;
-  k2_brick<L, S, BX, BY, NS, FORCE>(&tmap, args, b % nbx, (b / nbx) % nby, b / (nbx * nby));
+  k2_brick<L, S, BX, BY, NS, FORCE, L::Q == 9>(&tmap, args, b % nbx, (b / nbx) % nby, b / (nbx * nby));
 }
 
 // One launch per time step of many domains (a batch): a persistent grid whose
