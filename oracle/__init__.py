@@ -14,7 +14,9 @@ Two implementations live here:
   of the closed form, used to cross-check the C oracle.
 * ``lbm_oracle.c`` also holds the two-component colour-gradient step
   (section 2.1: relaxation + perturbation of the total set, recolouring of
-  each colour), written in the paper's order with its readings stated there.
+  each colour) and its near-contact interactions (section 2.2: flags of the
+  nodes around thin films of the continuous phase, a repulsive body force on
+  them), written in the paper's order with its readings stated there.
 * ``storage.py`` -- round-to-nearest-even of the shifted populations to the
   reduced storage formats (FP16, BF16), from the formats' definitions; with
   ``run_stored`` below it gives the exact reference of a reduced-precision run
@@ -67,6 +69,9 @@ class OrcCgCfg(ctypes.Structure):
         ("rho0", ctypes.c_double),
         ("sigma", ctypes.c_double),
         ("beta", ctypes.c_double),
+        ("nci_amp", ctypes.c_double),
+        ("nci_eps", ctypes.c_double),
+        ("nci_h", ctypes.c_int),
     ]
 
 
@@ -108,6 +113,7 @@ def lib():
             L.orc_cg_init.argtypes = [P(OrcCgCfg), dp, dp, dp, dp, dp]
             L.orc_cg_run.argtypes = [P(OrcCgCfg), dp, dp, ctypes.c_long, ctypes.c_int]
             L.orc_cg_fields.argtypes = [P(OrcCgCfg), dp, dp, dp, dp, dp]
+            L.orc_cg_nci_flags.argtypes = [P(OrcCgCfg), dp, ctypes.POINTER(ctypes.c_ubyte)]
             _lib = L
     return _lib
 
@@ -232,8 +238,10 @@ def run_stored(cfg: OrcCfg, f: np.ndarray, steps: int, storage: str, threads: in
 
 
 # ------------------------------------------------------------ colour gradient
-def make_cg_cfg(lattice, dims, tau, sigma, beta, rho0=1.0) -> OrcCgCfg:
-    """Two-component colour-gradient configuration (periodic box)."""
+def make_cg_cfg(lattice, dims, tau, sigma, beta, rho0=1.0, nci_amp=0.0, nci_eps=0.1, nci_h=1) -> OrcCgCfg:
+    """Two-component colour-gradient configuration (periodic box); nci_amp > 0
+    adds the near-contact interactions of section 2.2 (bulk threshold
+    nci_eps, sampling distance nci_h)."""
     if isinstance(lattice, str):
         lattice = LATTICE_NAMES[lattice]
     c = OrcCgCfg()
@@ -241,6 +249,7 @@ def make_cg_cfg(lattice, dims, tau, sigma, beta, rho0=1.0) -> OrcCgCfg:
     nx, ny, nz = (list(dims) + [1, 1])[:3]
     c.nx, c.ny, c.nz = int(nx), int(ny), int(nz)
     c.tau, c.rho0, c.sigma, c.beta = float(tau), float(rho0), float(sigma), float(beta)
+    c.nci_amp, c.nci_eps, c.nci_h = float(nci_amp), float(nci_eps), int(nci_h)
     return c
 
 
@@ -292,6 +301,16 @@ def cg_fields(cfg: OrcCgCfg, fr, fb):
     assert lib().orc_cg_fields(ctypes.byref(cfg), _dp(np.ascontiguousarray(fr)), _dp(np.ascontiguousarray(fb)),
                                _dp(rr), _dp(rb), _dp(u)) == 0
     return rr, rb, u
+
+
+def cg_nci_flags(cfg: OrcCgCfg, phi) -> np.ndarray:
+    """Near-contact flags (uint8, 1 = force acts) of a phase field (section 2.2)."""
+    N = cfg.nx * cfg.ny * cfg.nz
+    phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(N)
+    fl = np.zeros(N, dtype=np.uint8)
+    if lib().orc_cg_nci_flags(ctypes.byref(cfg), _dp(phi), fl.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))) != 0:
+        raise ValueError("orc_cg_nci_flags rejected the configuration")
+    return fl
 
 
 def max_threads() -> int:

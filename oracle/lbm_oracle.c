@@ -413,6 +413,21 @@ int orc_init(const orc_cfg* cfg, const double* rho, const double* u, const doubl
 /*     both colours; the opposite signs keep f_R* + f_B* = g*, and the zero- */
 /*     velocity equilibrium is taken per unit density (t_a).                 */
 /*  4. each colour streams (pull, periodic wrap).                            */
+/* Near-contact interactions (section 2.2), when nci_amp > 0: before the     */
+/* collision every node is checked for a thin film of the continuous (blue) */
+/* phase between two interfaces, and flagged nodes collide with a body      */
+/* force (the forcing term of the single-component step):                  */
+/*   flag(y) = 1 if, for some direction a, the node x = y - h c_a is bulk    */
+/*   (phi(x) < -1 + eps) and both points sampled from it along the pair of  */
+/*   opposite directions, x + h c_a = y and x - h c_a, are not bulk          */
+/*   (phi > -1 + eps);                                                       */
+/*   F(y) = A rho_R(y) grad phi / |grad phi|  (0 where grad phi = 0).        */
+/* -- readings: the paper states the test from the bulk node ("flag the two  */
+/* points"); written from the flagged node it is race free.  "Larger than   */
+/* phi_bulk" is read as "not bulk" (a bulk minimum of phi would otherwise   */
+/* flag noise); the dispersed phase is red (phi > 0), and the force points  */
+/* along the interface normal into it, away from the film.  eps, h and A    */
+/* are parameters: the paper gives no values.                              */
 /* ======================================================================== */
 
 /* perturbation weights B_a by |c|^2 shell (they satisfy sum B = cs2 and
@@ -505,6 +520,32 @@ int orc_cg_fields(const orc_cg_cfg* cfg, const double* fr, const double* fb, dou
   return 0;
 }
 
+int orc_cg_nci_flags(const orc_cg_cfg* cfg, const double* phi, unsigned char* flags) {
+  lattice_t L;
+  if (cg_check(cfg, &L) < 0 || !phi || !flags || cfg->nci_h < 1) return -1;
+  const long nx = cfg->nx, ny = cfg->ny, nz = cfg->nz, N = nx * ny * nz;
+  const long h = cfg->nci_h;
+  const double bulk = -1.0 + cfg->nci_eps;
+#pragma omp parallel for schedule(static)
+  for (long idx = 0; idx < N; ++idx) {
+    const long x = idx % nx, y = (idx / nx) % ny, z = idx / (nx * ny);
+    unsigned char fl = 0;
+    if (phi[idx] > bulk) {
+      for (int a = 1; a < L.q && !fl; ++a) {
+        /* the bulk candidate one sampling distance upstream, and the point
+         * one further sampling distance beyond it */
+        const long x1 = cg_wrap(x - h * L.c[a][0], nx), y1 = cg_wrap(y - h * L.c[a][1], ny),
+                   z1 = cg_wrap(z - h * L.c[a][2], nz);
+        const long x2 = cg_wrap(x - 2 * h * L.c[a][0], nx), y2 = cg_wrap(y - 2 * h * L.c[a][1], ny),
+                   z2 = cg_wrap(z - 2 * h * L.c[a][2], nz);
+        if (phi[x1 + nx * (y1 + ny * z1)] < bulk && phi[x2 + nx * (y2 + ny * z2)] > bulk) fl = 1;
+      }
+    }
+    flags[idx] = fl;
+  }
+  return 0;
+}
+
 int orc_cg_run(const orc_cg_cfg* cfg, double* fr, double* fb, long steps, int nthreads) {
   lattice_t L;
   if (cg_check(cfg, &L) < 0 || !fr || !fb || steps < 0) return -1;
@@ -519,12 +560,15 @@ int orc_cg_run(const orc_cg_cfg* cfg, double* fr, double* fb, long steps, int nt
   double B[QMAX];
   for (int a = 0; a < q; ++a)
     B[a] = cg_B_of(cfg->lattice, L.c[a][0] * L.c[a][0] + L.c[a][1] * L.c[a][1] + L.c[a][2] * L.c[a][2]);
+  const int nci = cfg->nci_amp != 0.0;
+  if (nci && cfg->nci_h < 1) return -1;
   double* phi = (double*)malloc(sizeof(double) * N);
   double* grad = (double*)malloc(sizeof(double) * 3 * N);
   double* pr = (double*)malloc(sizeof(double) * q * N);
   double* pb = (double*)malloc(sizeof(double) * q * N);
-  if (!phi || !grad || !pr || !pb) {
-    free(phi); free(grad); free(pr); free(pb);
+  unsigned char* flags = (unsigned char*)calloc((size_t)N, 1);
+  if (!phi || !grad || !pr || !pb || !flags) {
+    free(phi); free(grad); free(pr); free(pb); free(flags);
     return -2;
   }
   for (long t = 0; t < steps; ++t) {
@@ -539,6 +583,7 @@ int orc_cg_run(const orc_cg_cfg* cfg, double* fr, double* fb, long steps, int nt
       phi[idx] = (rr - rb) / (rr + rb);
     }
     orc_cg_gradient(cfg, phi, grad);
+    if (nci) orc_cg_nci_flags(cfg, phi, flags);
     /* collide: relax + perturb the total set, then recolour */
 #pragma omp parallel for schedule(static)
     for (long idx = 0; idx < N; ++idx) {
@@ -550,8 +595,6 @@ int orc_cg_run(const orc_cg_cfg* cfg, double* fr, double* fb, long steps, int nt
         rb += b;
         g[a] = r + b;
       }
-      orc_cfg one = {cfg->lattice, 1, 1, 1, cfg->tau, cfg->rho0, {0, 0, 0}, {0, 0, 0, 0, 0, 0}, {{0}}};
-      collide(&L, &one, g, gpc, 0);
       const double rho = rr + rb;
       double gv[3] = {0, 0, 0}, g2 = 0.0;
       for (int al = 0; al < d; ++al) {
@@ -559,6 +602,10 @@ int orc_cg_run(const orc_cg_cfg* cfg, double* fr, double* fb, long steps, int nt
         g2 += gv[al] * gv[al];
       }
       const double gn = sqrt(g2);
+      orc_cfg one = {cfg->lattice, 1, 1, 1, cfg->tau, cfg->rho0, {0, 0, 0}, {0, 0, 0, 0, 0, 0}, {{0}}};
+      if (nci && flags[idx] && gn > 0.0)
+        for (int al = 0; al < d; ++al) one.force[al] = cfg->nci_amp * rr * gv[al] / gn;
+      collide(&L, &one, g, gpc, 0);
       for (int a = 0; a < q; ++a) {
         double cg = 0.0, c2 = 0.0;
         for (int al = 0; al < d; ++al) {
@@ -588,6 +635,6 @@ int orc_cg_run(const orc_cg_cfg* cfg, double* fr, double* fb, long steps, int nt
       }
     }
   }
-  free(phi); free(grad); free(pr); free(pb);
+  free(phi); free(grad); free(pr); free(pb); free(flags);
   return 0;
 }

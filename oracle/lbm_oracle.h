@@ -84,6 +84,10 @@ typedef struct {
   double tau, rho0;
   double sigma;         /* surface tension parameter of the perturbation */
   double beta;          /* recolouring parameter (interface width) */
+  /* near-contact interactions (section 2.2); nci_amp = 0 switches them off */
+  double nci_amp;       /* force amplitude A: F = A rho_R n at flagged nodes */
+  double nci_eps;       /* bulk threshold: a node is bulk if phi < -1 + eps */
+  int nci_h;            /* sampling distance along the lattice directions */
 } orc_cg_cfg;
 int orc_cg_weights(int lattice, double* B);  /* perturbation weights B_a; returns q */
 int orc_cg_gradient(const orc_cg_cfg* cfg, const double* phi, double* grad);  /* [d][N] */
@@ -92,6 +96,9 @@ int orc_cg_init(const orc_cg_cfg* cfg, const double* rho_r, const double* rho_b,
 int orc_cg_run(const orc_cg_cfg* cfg, double* fr, double* fb, long steps, int nthreads);
 int orc_cg_fields(const orc_cg_cfg* cfg, const double* fr, const double* fb, double* rho_r, double* rho_b,
                   double* u);
+/* Near-contact flags of a phase field phi[N] (1 = the repulsive force acts
+ * on the node in the next collision). */
+int orc_cg_nci_flags(const orc_cg_cfg* cfg, const double* phi, unsigned char* flags);
 
 /* Number of OpenMP threads a parallel region would use (0 without OpenMP). */
 int orc_max_threads(void);
