@@ -64,6 +64,10 @@ WORKLOADS = {
                          drops=2000, radius=(8, 24)),
     "cg_d3q19_256": dict(lattice="D3Q19", dims=(256, 256, 256), tau=1.0, flow="cg", sigma=0.01, beta=0.7,
                          drops=300, radius=(6, 16)),
+    # the same 2D emulsion with near-contact interactions (section 2.2):
+    # amplitude 0.01, bulk threshold eps = 0.1, sampling distance h = 2
+    "cg_d2q9_4096_nci": dict(lattice="D2Q9", dims=(4096, 4096, 1), tau=1.0, flow="cg", sigma=0.01, beta=0.7,
+                             drops=2000, radius=(8, 24), nci=(0.01, 0.1, 2)),
 }
 Q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}
@@ -634,6 +638,8 @@ def run_cg(args, w):
     stream = torch.cuda.Stream()
     s = CGSolver(lattice, dims[:2] if dims[2] == 1 else dims, w["tau"], w["sigma"], w["beta"], storage=args.storage,
                  stream=stream)
+    if "nci" in w:
+        s.set_nci(*w["nci"])
     rr, rb = emulsion_fields(w, torch)
     s.init(rr, rb)
     del rr, rb
@@ -673,6 +679,7 @@ def run_cg(args, w):
             "data": "synthetic",
             "config": {"workload": args.workload, "lattice": lattice, "dims": list(dims), "tau": w["tau"],
                        "sigma": w["sigma"], "beta": w["beta"], "drops": w["drops"], "storage": args.storage,
+                       "nci": (dict(zip(("amplitude", "eps", "h"), w["nci"])) if "nci" in w else None),
                        "launches_per_step": 3, "l2_flush": "inputs larger than L2",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

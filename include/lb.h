@@ -320,6 +320,20 @@ LB_API int lb_cg_fields(lb_cg* c, double* rho_r, double* rho_b, double* u, int32
 LB_API int lb_cg_sync(lb_cg* c);
 LB_API void lb_cg_destroy(lb_cg* c);
 
+/* Near-contact interactions (section 2.2): a short-range repulsion that keeps
+ * approaching interfaces from coalescing.  Before each collision a node y is
+ * flagged if, for some direction a, the node y - h c_a is bulk continuous
+ * (blue) phase, phi < -1 + eps, while y and y - 2h c_a are not (the paper's
+ * test from the bulk node, evaluated at the flagged node); a flagged node
+ * collides with the body force F = amplitude * rho_R * grad phi / |grad phi|
+ * (towards the dispersed, red phase; the forcing of the single-component
+ * step), so the force grows as the films between interfaces thin.  The paper
+ * gives no values for eps, h or the amplitude.  amplitude = 0 (the state after
+ * lb_cg_create) switches the interactions off; amplitude >= 0 and finite,
+ * 0 < eps < 2, h >= 1 with 2h <= every periodic extent, else LB_E_INVAL.
+ * Takes effect from the next lb_cg_step. */
+LB_API int lb_cg_set_nci(lb_cg* c, double amplitude, double eps, int32_t h);
+
 /* Self-test of the bounded wait that every kernel applies to its mbarrier
  * waits (the paper has no counterpart: failure detection of this library).
  * Launches one tiny kernel that waits on a barrier nothing completes, for at

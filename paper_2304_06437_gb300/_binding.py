@@ -149,6 +149,7 @@ SIGNATURES = {
     "lb_cg_fields": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32]),
     "lb_cg_sync": (ctypes.c_int, [_vp]),
     "lb_cg_destroy": (None, [_vp]),
+    "lb_cg_set_nci": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int32]),
     "lb_selftest_timeout": (ctypes.c_int, [ctypes.c_int64, _i64p]),
     "lb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lb_abi_version": (ctypes.c_int, []),

@@ -20,8 +20,19 @@
 // Each colour is stored shifted by half the rest population, t_a rho0 / 2,
 // so that g is stored shifted by t_a rho0 as in the single-component path.
 // Periodic box only; D2Q9 and D3Q19; FP64 or FP32 storage and arithmetic.
+//
+// Near-contact interactions (section 2.2), when switched on: the gradient
+// launch also flags node y if, for some direction a, the node y - h c_a is
+// bulk (phi < -1 + eps) and both y and y - 2h c_a are not -- the paper's test
+// from the bulk node, written from the flagged node so that every thread
+// writes only its own node -- and a flagged node's relaxation coefficients
+// are recomputed from its own populations with the body force
+// F = A rho_R grad phi / |grad phi| (the forcing of the single-component
+// step).  No thread reads coefficients in that launch, and populations are
+// only written by the rebuild launch after it.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -88,8 +99,18 @@ __global__ void __launch_bounds__(kCgThreads) cg_moments_kernel(CgGeom g, const 
   }
 }
 
-template <class L, class R>
-__global__ void __launch_bounds__(kCgThreads) cg_gradient_kernel(CgGeom g, R* __restrict__ fld) {
+// near-contact parameters of the gradient launch
+template <class R>
+struct CgNci {
+  R amp, bulk, half_rho0;  // A, -1 + eps, rho0 / 2
+  int h;
+};
+
+template <class L, class S, class R, bool NCI>
+__global__ void __launch_bounds__(kCgThreads) cg_gradient_kernel(CgGeom g, R* __restrict__ fld,
+                                                                  const S* __restrict__ fr,
+                                                                  const S* __restrict__ fb, Phys<R> ph,
+                                                                  CgNci<R> nci) {
   const R* phi = fld + F_PHI * g.n;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < g.n; i += int64_t(gridDim.x) * blockDim.x) {
     const int x = int(i % g.nx), y = int((i / g.nx) % g.ny), z = int(i / (int64_t(g.nx) * g.ny));
@@ -110,6 +131,45 @@ __global__ void __launch_bounds__(kCgThreads) cg_gradient_kernel(CgGeom g, R* __
     const R gn = sqrt(g2);
     fld[F_GN * g.n + i] = gn;
     for (int al = 0; al < 3; ++al) fld[(F_N + al) * g.n + i] = gn > R(0) ? gv[al] / gn : R(0);
+    if constexpr (NCI) {
+      bool flag = false;
+      if (phi[i] > nci.bulk) {
+        const int h = nci.h;
+        static_for<1, L::Q>([&](auto A_) {
+          constexpr int a = decltype(A_)::value;
+          constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+          const R p1 = phi[cg_wrap_index(g, x - h * cx, y - h * cy, z - h * cz)];
+          const R p2 = phi[cg_wrap_index(g, x - 2 * h * cx, y - 2 * h * cy, z - 2 * h * cz)];
+          flag = flag || (p1 < nci.bulk && p2 > nci.bulk);
+        });
+      }
+      if (flag && gn > R(0)) {
+        R gt[L::Q];
+        R sr = R(0);
+        static_for<0, L::Q>([&](auto A_) {
+          constexpr int a = decltype(A_)::value;
+          const R r = load_as<S, R>(fr[a * g.n + i]), b = load_as<S, R>(fb[a * g.n + i]);
+          sr = sr + r;
+          gt[a] = r + b;
+        });
+        const R rr = sr + nci.half_rho0;  // rho_R
+        Phys<R> pf = ph;
+        for (int al = 0; al < 3; ++al) {
+          pf.F[al] = nci.amp * rr * (gv[al] / gn);
+          pf.hF[al] = R(0.5) * pf.F[al];
+        }
+        Mom<R> m;
+        moments<L, R, true>(gt, pf, m);
+        Coef<R> k;
+        coeffs<L, R, true>(m, pf, k);
+        fld[(F_COEF + 0) * g.n + i] = k.A;
+        for (int al = 0; al < 3; ++al) {
+          fld[(F_COEF + 1 + al) * g.n + i] = k.B[al];
+          fld[(F_COEF + 4 + al) * g.n + i] = k.C[al];
+          fld[(F_COEF + 7 + al) * g.n + i] = k.C2[al];
+        }
+      }
+    }
   }
 }
 
@@ -257,6 +317,8 @@ struct lb_cg {
   void* fb;
   void* fld;
   int64_t steps_done;
+  double nci_amp, nci_eps;  // near-contact interactions: off while nci_amp == 0
+  int nci_h;
 };
 
 using namespace lbgb;
@@ -448,7 +510,12 @@ int lb_cg_step(lb_cg* c, int64_t n) {
       const int grid = grid_of(c->g.n);
       cg_moments_kernel<L, S, R><<<grid, kCgThreads, 0, c->stream>>>(
           c->g, static_cast<const S*>(c->fr), static_cast<const S*>(c->fb), ph, R(0.5 * c->rho0), R(c->beta), fld);
-      cg_gradient_kernel<L, R><<<grid, kCgThreads, 0, c->stream>>>(c->g, fld);
+      const CgNci<R> nci{R(c->nci_amp), R(-1.0 + c->nci_eps), R(0.5 * c->rho0), c->nci_h};
+      if (c->nci_amp != 0.0)
+        cg_gradient_kernel<L, S, R, true><<<grid, kCgThreads, 0, c->stream>>>(
+            c->g, fld, static_cast<const S*>(c->fr), static_cast<const S*>(c->fb), ph, nci);
+      else
+        cg_gradient_kernel<L, S, R, false><<<grid, kCgThreads, 0, c->stream>>>(c->g, fld, nullptr, nullptr, ph, nci);
       cg_rebuild_kernel<L, S, R><<<grid, kCgThreads, 0, c->stream>>>(
           c->g, fld, R(2.25 * c->sigma / c->tau), R(0.5 * c->rho0), static_cast<S*>(c->fr), static_cast<S*>(c->fb));
     });
@@ -488,6 +555,18 @@ int lb_cg_fields(lb_cg* c, double* rho_r, double* rho_b, double* u, int32_t on_d
   }
   const int rc2 = rc_of(cudaStreamSynchronize(c->stream));
   return rc != LB_OK ? rc : rc2;
+}
+
+int lb_cg_set_nci(lb_cg* c, double amplitude, double eps, int32_t h) {
+  if (!c || !std::isfinite(amplitude) || amplitude < 0.0 || !(eps > 0.0) || !(eps < 2.0) || h < 1) return LB_E_INVAL;
+  // the sampled points lie up to 2h nodes away along every moving axis: one
+  // periodic wrap must reach them
+  const int lim = c->d == 2 ? std::min(c->g.nx, c->g.nz) : std::min(c->g.nx, std::min(c->g.ny, c->g.nz));
+  if (2 * int64_t(h) > lim) return LB_E_INVAL;
+  c->nci_amp = amplitude;
+  c->nci_eps = eps;
+  c->nci_h = h;
+  return LB_OK;
 }
 
 int lb_cg_sync(lb_cg* c) {

@@ -272,6 +272,12 @@ class CGSolver:
                                                 ctypes.c_void_p(fb.ctypes.data), 0), "lb_cg_get_populations")
         return fr, fb
 
+    def set_nci(self, amplitude, eps=0.1, h=1):
+        """Near-contact interactions (section 2.2): repulsive force
+        amplitude * rho_R * n on nodes flagged around thin films of the blue
+        phase (bulk: phi < -1 + eps; sampling distance h); 0 switches off."""
+        B.check(self._lib.lb_cg_set_nci(self._c, float(amplitude), float(eps), int(h)), "lb_cg_set_nci")
+
     def step(self, n=1):
         B.check(self._lib.lb_cg_step(self._c, int(n)), "lb_cg_step")
 
