@@ -37,6 +37,7 @@ struct FusedPlan {
   int wbuf;                // shared window buffers (2: one barrier per plane)
   int xwarps;              // dedicated export warps (0: node-owning warps export)
   int npt;                 // nodes per thread (1 scalar, 2 paired FP32x2 kernel)
+  int ts;                  // 1: completed planes leave through a TMA store
   size_t smem_bytes;
 };
 

@@ -43,8 +43,9 @@ static int variant_lists(int lattice, const K1Variant* lists[2], int counts[2]) 
 }
 
 // The first compiled shape that matches (lattice, storage, bx, by, ns, wb,
-// nxw, npt); zero fields (negative nxw) match anything.
-static const K1Variant* find_variant(int lattice, int storage, int bx, int by, int ns, int wb, int nxw, int npt) {
+// nxw, npt, ts); zero fields (negative nxw, ts) match anything.
+static const K1Variant* find_variant(int lattice, int storage, int bx, int by, int ns, int wb, int nxw, int npt,
+                                     int ts) {
   const K1Variant* lists[2];
   int counts[2];
   const int nl = variant_lists(lattice, lists, counts);
@@ -58,22 +59,25 @@ static const K1Variant* find_variant(int lattice, int storage, int bx, int by, i
       if (wb > 0 && v.wb != wb) continue;
       if (nxw >= 0 && v.nxw != nxw) continue;
       if (npt > 0 && v.npt != npt) continue;
+      if (ts >= 0 && v.ts != ts) continue;
       return &v;
     }
   }
   return nullptr;
 }
 
-// Optional pipeline request from the environment, "NS,WB[,NXW[,NPT]]" (TMA
-// slots, window buffers, dedicated export warps, nodes per thread), used to
-// compare the compiled alternatives of a brick shape; 0 (-1 for NXW) = any.
-static void pipeline_request(int* ns, int* wb, int* nxw, int* npt) {
+// Optional pipeline request from the environment, "NS,WB[,NXW[,NPT[,TS]]]"
+// (TMA slots, window buffers, dedicated export warps, nodes per thread, TMA
+// store of completed planes), used to compare the compiled alternatives of a
+// brick shape; 0 (-1 for NXW and TS) = any.
+static void pipeline_request(int* ns, int* wb, int* nxw, int* npt, int* ts) {
   *ns = 0;
   *wb = 0;
   *nxw = -1;
   *npt = 0;
+  *ts = -1;
   const char* e = std::getenv("LB_FUSED_PIPELINE");
-  if (e) std::sscanf(e, "%d,%d,%d,%d", ns, wb, nxw, npt);
+  if (e) std::sscanf(e, "%d,%d,%d,%d,%d", ns, wb, nxw, npt, ts);
 }
 
 static int sm_count() {
@@ -114,6 +118,7 @@ static void fill_plan(const Geometry& g, const K1Variant* v, int req_bz, FusedPl
   p.wbuf = v->wb;
   p.xwarps = v->nxw;
   p.npt = v->npt;
+  p.ts = v->ts;
   p.smem_bytes = v->smem;
   p.nbx = (g.nx + p.bx - 1) / p.bx;
   p.nby = (g.ny + p.by - 1) / p.by;
@@ -140,9 +145,9 @@ static void fill_plan(const Geometry& g, const K1Variant* v, int req_bz, FusedPl
 bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPlan* plan) {
   const int rbx = tile_req ? tile_req[0] : 0;
   const int rby = tile_req ? tile_req[1] : 0;
-  int rns, rwb, rnxw, rnpt;
-  pipeline_request(&rns, &rwb, &rnxw, &rnpt);
-  const K1Variant* v = find_variant(g.lattice, storage, rbx, rby, rns, rwb, rnxw, rnpt);
+  int rns, rwb, rnxw, rnpt, rts;
+  pipeline_request(&rns, &rwb, &rnxw, &rnpt, &rts);
+  const K1Variant* v = find_variant(g.lattice, storage, rbx, rby, rns, rwb, rnxw, rnpt, rts);
   if (!v) return false;
   fill_plan(g, v, tile_req ? tile_req[2] : 0, plan);
   return true;
@@ -171,7 +176,7 @@ int k1_variants_for(int lattice, int storage, const void** out, int cap) {
 
 static const K1Variant* ctx_variant(lb_ctx* ctx) {
   return find_variant(ctx->lattice, ctx->storage, ctx->plan.bx, ctx->plan.by, ctx->plan.slots, ctx->plan.wbuf,
-                      ctx->plan.xwarps, ctx->plan.npt);
+                      ctx->plan.xwarps, ctx->plan.npt, ctx->plan.ts);
 }
 
 const K1Variant* k1_ctx_variant(lb_ctx* ctx) { return ctx_variant(ctx); }

@@ -633,7 +633,9 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
 #undef LB_RING_PUT
 }
 
-// One launch per time step of one domain: one CTA per brick column.
+// One launch per time step of one domain: one CTA per brick column.  D2Q9
+// sweeps three planes per loop trip and keeps three CTAs per SM (the register
+// cap that this implies holds the unrolled body without spills).
 template <class L, class S, int BX, int BY, int NS, bool FORCE>
 __global__ void __launch_bounds__(BX* BY / 2, (L::Q == 9 ? 3 : 1))
     k2_fused_step(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ K1Args<float> args) {

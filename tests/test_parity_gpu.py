@@ -254,11 +254,13 @@ def test_checkpoint_resume_is_bitwise(Solver, lat, storage):
         assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("storage,pipeline,slots", [("f32", "2,0,-1,0", 2), ("f16s", "4,0,-1,0,1", 4)])
 @pytest.mark.parametrize("fname", ["lid", "periodic", "duct"])
-def test_tma_store_variant_bitwise(Solver, fname, monkeypatch):
-    """The brick shape whose completed planes leave through a shared-memory
-    buffer and one TMA store (64 x 8, two-slot ring) gives the two-pass bits,
-    including ragged bricks whose out-of-range lanes the store drops."""
+def test_tma_store_variant_bitwise(Solver, fname, storage, pipeline, slots, monkeypatch):
+    """The brick shapes whose completed planes leave through a shared-memory
+    buffer and one TMA store (64 x 8; FP32 with a two-slot ring, FP16 with a
+    four-slot ring) give the two-pass bits, including ragged bricks whose
+    out-of-range lanes the store drops."""
     lat, dims = "D3Q19", (150, 30, 23)
     faces, wall_u = faces_for(lat, fname)
     force = (2e-5, 0, 1e-5) if fname == "duct" else (0, 0, 0)
@@ -266,11 +268,11 @@ def test_tma_store_variant_bitwise(Solver, fname, monkeypatch):
     outs = []
     for scheme, t in (("two_pass", None), ("fused", (64, 8, 5)), ("fused", (64, 8, 0))):
         if scheme == "fused":
-            monkeypatch.setenv("LB_FUSED_PIPELINE", "2,0,-1,0")
-        s = Solver(lat, dims, 0.58, faces=faces, wall_u=wall_u, storage="f32", scheme=scheme, force=force, tile=t)
+            monkeypatch.setenv("LB_FUSED_PIPELINE", pipeline)
+        s = Solver(lat, dims, 0.58, faces=faces, wall_u=wall_u, storage=storage, scheme=scheme, force=force, tile=t)
         monkeypatch.delenv("LB_FUSED_PIPELINE", raising=False)
         if scheme == "fused":
-            assert s.info()["tma_slots"] == 2 and s.info()["tile"][:2] == (64, 8)
+            assert s.info()["tma_slots"] == slots and s.info()["tile"][:2] == (64, 8)
         s.set_populations(np.ascontiguousarray(f0))
         s.step(9)
         outs.append(s.get_populations())
