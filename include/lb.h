@@ -127,7 +127,9 @@ LB_API int lb_create(int32_t lattice, const int64_t dims[3], double tau, const l
 /* Sets the state to f = f^eq(rho, u) + fhat^neq(pineq) - t_a c_a.F/(2 cs2):
  * Eq. equil plus the order-2 Hermite non-equilibrium part, shifted so that
  * the state reports u.  rho [N], u [d][N], pineq [3 or 6][N] or NULL (= 0).
- * All three are host (on_device = 0) or device (on_device = 1) FP64 arrays. */
+ * All three are host (on_device = 0) or device (on_device = 1) FP64 arrays.
+ * Host arrays cross a chunk of nodes at a time through one device buffer of
+ * at most 512 MB (pinned host memory moves at the copy engines' rate). */
 LB_API int lb_init_moments(lb_ctx* ctx, const double* rho, const double* u, const double* pineq,
                     int32_t on_device);
 
@@ -146,7 +148,9 @@ LB_API int lb_get_region(lb_ctx* ctx, const int64_t lo[3], const int64_t size[3]
 /* Enqueues n time steps on the context stream (asynchronous). */
 LB_API int lb_step(lb_ctx* ctx, int64_t n);
 
-/* Density rho [N] and velocity u [d][N] of the stored state (FP64 sums). */
+/* Density rho [N] and velocity u [d][N] of the stored state (FP64 sums).
+ * Either may be NULL.  Host outputs (on_device = 0) are filled a chunk of
+ * nodes at a time through one device buffer of at most 512 MB. */
 LB_API int lb_moments(lb_ctx* ctx, double* rho, double* u, int32_t on_device);
 
 /* FP64 on-device reductions over all nodes: total mass sum rho, total momentum

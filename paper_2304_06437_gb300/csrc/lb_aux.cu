@@ -72,29 +72,33 @@ __global__ void get_pop_kernel(Layout l, const S* __restrict__ ft, double* __res
 // f = f^eq(rho, u) + t_a (cc - cs2 I):Pi/(2 cs2^2) - t_a c.F/(2 cs2), in FP64,
 // stored shifted.  rho may be null (uniform rho_u), u may be null (uniform u_u).
 template <class L, class S, class R>
+// nodes [n0, n1); input node idx is element idx - n0 of each component, and
+// components lie cs elements apart
 __global__ void init_kernel(Layout l, S* __restrict__ ft, double rho0, const double* __restrict__ rho,
                             const double* __restrict__ u, const double* __restrict__ pineq, double rho_u,
-                            double ux_u, double uy_u, double uz_u, double Fx, double Fy, double Fz) {
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < l.n;
+                            double ux_u, double uy_u, double uz_u, double Fx, double Fy, double Fz, int64_t n0,
+                            int64_t n1, int64_t cs) {
+  for (int64_t idx = n0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n1;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t o = ioff(l, idx);
-    const double r = rho ? rho[idx] : rho_u;
+    const int64_t k0 = idx - n0;
+    const double r = rho ? rho[k0] : rho_u;
     double ui[3] = {0.0, 0.0, 0.0};
     const double uu[3] = {ux_u, uy_u, uz_u};
-    for (int k = 0; k < L::D; ++k) ui[user_axis<L>(k)] = u ? u[k * l.n + idx] : uu[k];
+    for (int k = 0; k < L::D; ++k) ui[user_axis<L>(k)] = u ? u[k * cs + k0] : uu[k];
     double P[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     if (pineq) {
       if (L::D == 2) {
-        P[0][0] = pineq[0 * l.n + idx];
-        P[2][2] = pineq[1 * l.n + idx];
-        P[0][2] = P[2][0] = pineq[2 * l.n + idx];
+        P[0][0] = pineq[0 * cs + k0];
+        P[2][2] = pineq[1 * cs + k0];
+        P[0][2] = P[2][0] = pineq[2 * cs + k0];
       } else {
-        P[0][0] = pineq[0 * l.n + idx];
-        P[1][1] = pineq[1 * l.n + idx];
-        P[2][2] = pineq[2 * l.n + idx];
-        P[0][1] = P[1][0] = pineq[3 * l.n + idx];
-        P[0][2] = P[2][0] = pineq[4 * l.n + idx];
-        P[1][2] = P[2][1] = pineq[5 * l.n + idx];
+        P[0][0] = pineq[0 * cs + k0];
+        P[1][1] = pineq[1 * cs + k0];
+        P[2][2] = pineq[2 * cs + k0];
+        P[0][1] = P[1][0] = pineq[3 * cs + k0];
+        P[0][2] = P[2][0] = pineq[4 * cs + k0];
+        P[1][2] = P[2][1] = pineq[5 * cs + k0];
       }
     }
     const double Fi[3] = {Fx, Fy, Fz};
@@ -106,13 +110,22 @@ __global__ void init_kernel(Layout l, S* __restrict__ ft, double rho0, const dou
     }
     static_for<0, L::Q>([&](auto A_) {
       constexpr int a = decltype(A_)::value;
-      constexpr int c[3] = {L::cx(a), L::cy(a), L::cz(a)};
+      // c.u, c.F and c.P.c with the components of c (0 or +-1) applied at
+      // compile time: zero terms are skipped, which leaves every sum exact
       double cu = 0.0, cF = 0.0, cPc = 0.0;
-      for (int i = 0; i < 3; ++i) {
-        cu += c[i] * ui[i];
-        cF += c[i] * Fi[i];
-        for (int j = 0; j < 3; ++j) cPc += c[i] * c[j] * P[i][j];
-      }
+      static_for<0, 3>([&](auto I_) {
+        constexpr int i = decltype(I_)::value;
+        constexpr int ci = comp<L>(i, a);
+        if constexpr (ci != 0) {
+          cu += ci > 0 ? ui[i] : -ui[i];
+          cF += ci > 0 ? Fi[i] : -Fi[i];
+        }
+        static_for<0, 3>([&](auto J_) {
+          constexpr int j = decltype(J_)::value;
+          constexpr int cc = ci * comp<L>(j, a);
+          if constexpr (cc != 0) cPc += cc > 0 ? P[i][j] : -P[i][j];
+        });
+      });
       const double w = weight<L>(a);
       const double v = w * (drho + rho0 * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq)) +
                        w * 4.5 * (cPc - trP / 3.0) - w * 1.5 * cF;
@@ -122,9 +135,11 @@ __global__ void init_kernel(Layout l, S* __restrict__ ft, double rho0, const dou
 }
 
 template <class L, class S, class R>
+// nodes [n0, n1) into element idx - n0 of each output component (cs apart)
 __global__ void moments_kernel(Layout l, const S* __restrict__ ft, double rho0, double Fx, double Fy, double Fz,
-                               double* __restrict__ rho, double* __restrict__ u) {
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < l.n;
+                               double* __restrict__ rho, double* __restrict__ u, int64_t n0, int64_t n1,
+                               int64_t cs) {
+  for (int64_t idx = n0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n1;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t o = ioff(l, idx);
     double dr = 0.0, j[3] = {0.0, 0.0, 0.0};
@@ -133,16 +148,16 @@ __global__ void moments_kernel(Layout l, const S* __restrict__ ft, double rho0, 
       const double v = static_cast<double>(load_as<S, R>(ft[a * l.vol + o]));
       constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
       dr += v;
-      j[0] += cx * v;
-      j[1] += cy * v;
-      j[2] += cz * v;
+      if constexpr (cx != 0) j[0] += cx > 0 ? v : -v;  // zero terms skipped: the sums are unchanged
+      if constexpr (cy != 0) j[1] += cy > 0 ? v : -v;
+      if constexpr (cz != 0) j[2] += cz > 0 ? v : -v;
     });
-    if (rho) rho[idx] = rho0 + dr;
+    if (rho) rho[idx - n0] = rho0 + dr;
     if (u) {
       const double Fi[3] = {Fx, Fy, Fz};
       for (int k = 0; k < L::D; ++k) {
         const int ax = user_axis<L>(k);
-        u[k * l.n + idx] = (j[ax] + 0.5 * Fi[ax]) / rho0;
+        u[k * cs + (idx - n0)] = (j[ax] + 0.5 * Fi[ax]) / rho0;
       }
     }
   }
@@ -187,9 +202,9 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(Layout l, const S* __r
       bad |= !isfinite(v);
       constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
       dr += v;
-      j[0] += cx * v;
-      j[1] += cy * v;
-      j[2] += cz * v;
+      if constexpr (cx != 0) j[0] += cx > 0 ? v : -v;  // zero terms skipped: the sums are unchanged
+      if constexpr (cy != 0) j[1] += cy > 0 ? v : -v;
+      if constexpr (cz != 0) j[2] += cz > 0 ? v : -v;
     });
     acc[0] += rho0 + dr;
     acc[1] += j[0];
@@ -273,8 +288,10 @@ cudaError_t aux_get_populations(lb_ctx* ctx, double* f_dev) {
 }
 
 static cudaError_t launch_init(lb_ctx* ctx, const double* rho, const double* u, const double* pineq, double rho_u,
-                               const double uu[3]) {
+                               const double uu[3], int64_t n0 = 0, int64_t n1 = -1, int64_t cs = -1) {
   const Layout l = layout_of(ctx->g);
+  if (n1 < 0) n1 = l.n;
+  if (cs < 0) cs = l.n;
   // the force is applied in internal axes inside the kernel
   const double* F = ctx->g.force;
   dispatch_lattice(ctx->lattice, [&](auto Lt) {
@@ -282,8 +299,9 @@ static cudaError_t launch_init(lb_ctx* ctx, const double* rho, const double* u, 
     dispatch_storage(ctx->storage, [&](auto St, auto Rt) {
       using S = typename decltype(St)::type;
       using R = typename decltype(Rt)::type;
-      init_kernel<L, S, R><<<grid_for(l.n), kThreads, 0, ctx->stream>>>(
-          l, static_cast<S*>(ctx->f), ctx->g.rho0, rho, u, pineq, rho_u, uu[0], uu[1], uu[2], F[0], F[1], F[2]);
+      init_kernel<L, S, R><<<grid_for(n1 - n0), kThreads, 0, ctx->stream>>>(
+          l, static_cast<S*>(ctx->f), ctx->g.rho0, rho, u, pineq, rho_u, uu[0], uu[1], uu[2], F[0], F[1], F[2], n0,
+          n1, cs);
     });
   });
   return cudaGetLastError();
@@ -298,7 +316,18 @@ cudaError_t aux_init_uniform(lb_ctx* ctx, double rho, const double u_user[3]) {
   return launch_init(ctx, nullptr, nullptr, nullptr, rho, u_user);
 }
 
+cudaError_t aux_init_moments_range(lb_ctx* ctx, const double* rho, const double* u, const double* pineq, int64_t n0,
+                                   int64_t n1, int64_t cs) {
+  const double zero[3] = {0, 0, 0};
+  return launch_init(ctx, rho, u, pineq, ctx->g.rho0, zero, n0, n1, cs);
+}
+
 cudaError_t aux_moments(lb_ctx* ctx, double* rho, double* u) {
+  return aux_moments_range(ctx, rho, u, 0, int64_t(ctx->g.nx) * ctx->g.ny * ctx->g.nz,
+                           int64_t(ctx->g.nx) * ctx->g.ny * ctx->g.nz);
+}
+
+cudaError_t aux_moments_range(lb_ctx* ctx, double* rho, double* u, int64_t n0, int64_t n1, int64_t cs) {
   const Layout l = layout_of(ctx->g);
   const double* F = ctx->g.force;
   dispatch_lattice(ctx->lattice, [&](auto Lt) {
@@ -306,8 +335,8 @@ cudaError_t aux_moments(lb_ctx* ctx, double* rho, double* u) {
     dispatch_storage(ctx->storage, [&](auto St, auto Rt) {
       using S = typename decltype(St)::type;
       using R = typename decltype(Rt)::type;
-      moments_kernel<L, S, R><<<grid_for(l.n), kThreads, 0, ctx->stream>>>(
-          l, static_cast<const S*>(ctx->f), ctx->g.rho0, F[0], F[1], F[2], rho, u);
+      moments_kernel<L, S, R><<<grid_for(n1 - n0), kThreads, 0, ctx->stream>>>(
+          l, static_cast<const S*>(ctx->f), ctx->g.rho0, F[0], F[1], F[2], rho, u, n0, n1, cs);
     });
   });
   return cudaGetLastError();

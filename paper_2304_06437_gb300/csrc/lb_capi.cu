@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -75,6 +76,10 @@ int make_tensor_map(lb_ctx* ctx) {
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? LB_OK : LB_E_CUDA;
 }
+
+// Host moment fields cross to and from the device through a buffer of at
+// most this size, one chunk of nodes at a time.
+constexpr size_t kChunkBytes = size_t(512) << 20;
 
 // Stage a host (or device) FP64 input to device memory on the context stream.
 struct Staged {
@@ -397,6 +402,35 @@ int lb_init_moments(lb_ctx* ctx, const double* rho, const double* u, const doubl
   const size_t N = size_t(ctx->n_nodes);
   const int d = ctx->g.d;
   const int np = d == 2 ? 3 : 6;
+  if (!on_device) {
+    // host fields: a chunk of nodes at a time through one bounded device
+    // buffer (one copy per component), converted as each chunk lands
+    const int ncomp = 1 + d + (pineq ? np : 0);
+    const size_t C = std::max<size_t>(1, std::min(N, kChunkBytes / (size_t(ncomp) * sizeof(double))));
+    double* buf = nullptr;
+    LB_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&buf), C * ncomp * sizeof(double), ctx->stream));
+    int rc = LB_OK;
+    for (size_t n0 = 0; n0 < N && rc == LB_OK; n0 += C) {
+      const size_t cnt = std::min(C, N - n0);
+      double* br = buf;
+      double* bu = buf + C;
+      double* bp = buf + C * (1 + d);
+      rc = cuda_status(cudaMemcpyAsync(br, rho + n0, cnt * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+      for (int k = 0; k < d && rc == LB_OK; ++k)
+        rc = cuda_status(cudaMemcpyAsync(bu + k * C, u + k * N + n0, cnt * sizeof(double), cudaMemcpyHostToDevice,
+                                         ctx->stream));
+      for (int k = 0; pineq && k < np && rc == LB_OK; ++k)
+        rc = cuda_status(cudaMemcpyAsync(bp + k * C, pineq + k * N + n0, cnt * sizeof(double),
+                                         cudaMemcpyHostToDevice, ctx->stream));
+      if (rc == LB_OK)
+        rc = cuda_status(aux_init_moments_range(ctx, br, bu, pineq ? bp : nullptr, int64_t(n0), int64_t(n0 + cnt),
+                                                int64_t(C)));
+    }
+    cudaFreeAsync(buf, ctx->stream);
+    if (rc == LB_OK) rc = after_state_change(ctx);
+    const int rc2 = cuda_status(cudaStreamSynchronize(ctx->stream));
+    return rc != LB_OK ? rc : rc2;
+  }
   Staged sr, su, sp;
   int rc = stage_in(ctx, rho, N, on_device, &sr);
   if (rc == LB_OK) rc = stage_in(ctx, u, N * d, on_device, &su);
@@ -502,13 +536,21 @@ int lb_moments(lb_ctx* ctx, double* rho, double* u, int32_t on_device) {
     if (rc == LB_OK) rc = cuda_status(cudaStreamSynchronize(ctx->stream));
     return rc;
   }
+  // a chunk of nodes at a time through one bounded device buffer
+  const size_t C = std::max<size_t>(1, std::min(N, kChunkBytes / ((1 + d) * sizeof(double))));
   double* tmp = nullptr;
-  LB_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (1 + d) * N * sizeof(double), ctx->stream));
-  int rc = cuda_status(aux_moments(ctx, tmp, tmp + N));
-  if (rc == LB_OK && rho)
-    rc = cuda_status(cudaMemcpyAsync(rho, tmp, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  if (rc == LB_OK && u)
-    rc = cuda_status(cudaMemcpyAsync(u, tmp + N, d * N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  LB_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (1 + d) * C * sizeof(double), ctx->stream));
+  int rc = LB_OK;
+  for (size_t n0 = 0; n0 < N && rc == LB_OK; n0 += C) {
+    const size_t cnt = std::min(C, N - n0);
+    rc = cuda_status(aux_moments_range(ctx, rho ? tmp : nullptr, u ? tmp + C : nullptr, int64_t(n0),
+                                       int64_t(n0 + cnt), int64_t(C)));
+    if (rc == LB_OK && rho)
+      rc = cuda_status(cudaMemcpyAsync(rho + n0, tmp, cnt * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    for (int k = 0; u && k < d && rc == LB_OK; ++k)
+      rc = cuda_status(cudaMemcpyAsync(u + k * N + n0, tmp + C + k * C, cnt * sizeof(double),
+                                       cudaMemcpyDeviceToHost, ctx->stream));
+  }
   cudaFreeAsync(tmp, ctx->stream);
   const int rc2 = cuda_status(cudaStreamSynchronize(ctx->stream));
   return rc != LB_OK ? rc : rc2;

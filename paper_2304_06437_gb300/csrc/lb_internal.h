@@ -100,6 +100,11 @@ cudaError_t aux_get_populations(lb_ctx* ctx, double* f_dev);
 cudaError_t aux_init_moments(lb_ctx* ctx, const double* rho, const double* u, const double* pineq);
 cudaError_t aux_init_uniform(lb_ctx* ctx, double rho, const double u_user[3]);
 cudaError_t aux_moments(lb_ctx* ctx, double* rho, double* u);
+// the same for nodes [n0, n1) only, with buffers holding element idx - n0 of
+// each component and components cs elements apart
+cudaError_t aux_init_moments_range(lb_ctx* ctx, const double* rho, const double* u, const double* pineq, int64_t n0,
+                                   int64_t n1, int64_t cs);
+cudaError_t aux_moments_range(lb_ctx* ctx, double* rho, double* u, int64_t n0, int64_t n1, int64_t cs);
 cudaError_t aux_get_region(lb_ctx* ctx, const int64_t lo[3], const int64_t size[3], double* f_dev);
 cudaError_t aux_reduce(lb_ctx* ctx, double* host_out /* mass, mom[3], du2, u2, nonfinite */,
                        bool residual);

@@ -225,6 +225,39 @@ def test_init_moments_device_buffers_and_readback(Solver):
     s.close()
 
 
+def test_host_moment_fields_cross_in_chunks(Solver):
+    """Host moment fields larger than the library's transfer buffer (512 MB:
+    3 chunks in with the momentum flux, 2 out) give exactly the bits of the
+    same fields passed as device buffers, on both the way in
+    (lb_init_moments) and the way out (lb_moments)."""
+    import torch
+    dims = (272, 256, 256)
+    N = dims[0] * dims[1] * dims[2]
+    g = torch.Generator(device="cuda").manual_seed(5)
+    rho_d = 1.0 + 0.01 * torch.rand(N, dtype=torch.float64, device="cuda", generator=g)
+    u_d = 0.02 * (torch.rand((3, N), dtype=torch.float64, device="cuda", generator=g) - 0.5)
+    p_d = 1e-4 * (torch.rand((6, N), dtype=torch.float64, device="cuda", generator=g) - 0.5)
+    rho_h, u_h, p_h = rho_d.cpu().numpy(), u_d.cpu().numpy(), p_d.cpu().numpy()
+    outs = []
+    for host in (False, True):
+        s = Solver("D3Q19", dims, 0.7, storage="f32")
+        if host:
+            s.init_moments(rho_h, u_h, p_h)
+            r, uu = s.moments()
+        else:
+            s.init_moments(rho_d, u_d, p_d)
+            r = torch.empty(N, dtype=torch.float64, device="cuda")
+            uu = torch.empty((3, N), dtype=torch.float64, device="cuda")
+            s.moments(r, uu)
+            torch.cuda.synchronize()
+            r, uu = r.cpu().numpy(), uu.cpu().numpy()
+        outs.append((s.get_region((0, 0, 0), dims), r, uu))
+        s.close()
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+    assert np.abs(outs[1][1] - rho_h).max() < 1e-6
+
+
 @pytest.mark.parametrize("lat,storage", [("D3Q19", "f32"), ("D3Q27", "f16s"), ("D2Q9", "bf16s"), ("D3Q19", "f64")])
 def test_checkpoint_resume_is_bitwise(Solver, lat, storage):
     """Checkpoint (lb_get_populations) and resume in a fresh context
