@@ -108,10 +108,16 @@ __global__ void init_kernel(Layout l, S* __restrict__ ft, double rho0, const dou
       usq += ui[k] * ui[k];
       trP += P[k][k];
     }
-    static_for<0, L::Q>([&](auto A_) {
-      constexpr int a = decltype(A_)::value;
+    // f_a = t_a [drho + rho0 (3 c.u + 4.5 (c.u)^2 - 1.5 u.u) + 4.5 (c.P.c - tr P / 3)
+    //           - 1.5 c.F]: a velocity pair {a, abar} shares the even part
+    // and takes the odd part (c.u, c.F) with opposite signs
+    const double ev0 = drho - 1.5 * rho0 * usq - 1.5 * trP;
+    ft[0 * l.vol + o] = store_as<S, R>(static_cast<R>(weight<L>(0) * ev0));
+    static_for<0, n_pairs<L>()>([&](auto P_) {
+      constexpr int a = pair_first<L>(decltype(P_)::value);
+      constexpr int b = L::opp(a);
       // c.u, c.F and c.P.c with the components of c (0 or +-1) applied at
-      // compile time: zero terms are skipped, which leaves every sum exact
+      // compile time
       double cu = 0.0, cF = 0.0, cPc = 0.0;
       static_for<0, 3>([&](auto I_) {
         constexpr int i = decltype(I_)::value;
@@ -127,9 +133,10 @@ __global__ void init_kernel(Layout l, S* __restrict__ ft, double rho0, const dou
         });
       });
       const double w = weight<L>(a);
-      const double v = w * (drho + rho0 * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq)) +
-                       w * 4.5 * (cPc - trP / 3.0) - w * 1.5 * cF;
-      ft[a * l.vol + o] = store_as<S, R>(static_cast<R>(v));
+      const double even = w * (ev0 + 4.5 * (rho0 * cu * cu + cPc));
+      const double odd = w * (3.0 * rho0 * cu - 1.5 * cF);
+      ft[a * l.vol + o] = store_as<S, R>(static_cast<R>(even + odd));
+      ft[b * l.vol + o] = store_as<S, R>(static_cast<R>(even - odd));
     });
   }
 }
