@@ -136,6 +136,14 @@ def test_cg_nci_matches_oracle(lb, lat, storage, ftol, tol):
     fr0, fb0 = oracle.cg_init(cfg, rr, rb, u)
     R0, B0, _ = oracle.cg_fields(cfg, fr0, fb0)
     assert oracle.cg_nci_flags(cfg, (R0 - B0) / (R0 + B0)).sum() > 0
+    # the flags are decisions taken in each side's precision: every phase
+    # value of the compared steps lies far enough from the bulk threshold
+    # that FP32 and FP64 take the same ones
+    fr, fb = fr0, fb0
+    for _ in range(20):
+        Rk, Bk, _ = oracle.cg_fields(cfg, fr, fb)
+        assert np.abs((Rk - Bk) / (Rk + Bk) - (-1.0 + eps)).min() > 1e-4
+        fr, fb = oracle.cg_run(cfg, fr, fb, 1)
     with lb.CGSolver(lat, dims, tau, sigma, beta, storage=storage) as s:
         s.set_nci(amp, eps, h)
         s.set_populations(np.ascontiguousarray(fr0), np.ascontiguousarray(fb0))
