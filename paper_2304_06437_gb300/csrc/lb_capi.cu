@@ -78,8 +78,35 @@ int make_tensor_map(lb_ctx* ctx) {
 }
 
 // Host moment fields cross to and from the device through a buffer of at
-// most this size, one chunk of nodes at a time.
+// most this size, in two halves: while the context stream converts the chunk
+// in one half, a copy stream moves the next (or previous) chunk through the
+// other.
 constexpr size_t kChunkBytes = size_t(512) << 20;
+
+// The copy stream and the per-half events of one host transfer.  Every
+// operation on the copy stream is waited for by the context stream before
+// the transfer returns, so destroying them afterwards is safe.
+struct CopyLane {
+  cudaStream_t s = nullptr;
+  cudaEvent_t ready[2] = {nullptr, nullptr};  // half filled (in) / emptied (out)
+  cudaEvent_t done[2] = {nullptr, nullptr};   // half consumed (in) / filled (out)
+  cudaError_t init() {
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaEventCreateWithFlags(&ready[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming);
+    }
+    return e;
+  }
+  ~CopyLane() {
+    if (s) cudaStreamSynchronize(s);
+    for (int k = 0; k < 2; ++k) {
+      if (ready[k]) cudaEventDestroy(ready[k]);
+      if (done[k]) cudaEventDestroy(done[k]);
+    }
+    if (s) cudaStreamDestroy(s);
+  }
+};
 
 // Stage a host (or device) FP64 input to device memory on the context stream.
 struct Staged {
@@ -403,29 +430,45 @@ int lb_init_moments(lb_ctx* ctx, const double* rho, const double* u, const doubl
   const int d = ctx->g.d;
   const int np = d == 2 ? 3 : 6;
   if (!on_device) {
-    // host fields: a chunk of nodes at a time through one bounded device
-    // buffer (one copy per component), converted as each chunk lands
+    // host fields: chunks of nodes through the two halves of one bounded
+    // device buffer (one copy per component on the copy stream), each chunk
+    // converted on the context stream as it lands
     const int ncomp = 1 + d + (pineq ? np : 0);
-    const size_t C = std::max<size_t>(1, std::min(N, kChunkBytes / (size_t(ncomp) * sizeof(double))));
+    const size_t C = std::max<size_t>(1, std::min(N, kChunkBytes / (2 * size_t(ncomp) * sizeof(double))));
+    CopyLane lane;
+    LB_TRY_CUDA(lane.init());
     double* buf = nullptr;
-    LB_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&buf), C * ncomp * sizeof(double), ctx->stream));
-    int rc = LB_OK;
-    for (size_t n0 = 0; n0 < N && rc == LB_OK; n0 += C) {
+    LB_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&buf), 2 * C * ncomp * sizeof(double), ctx->stream));
+    // the copy stream starts after the allocation (and after the work
+    // already queued on the context stream)
+    int rc = cuda_status(cudaEventRecord(lane.done[1], ctx->stream));
+    if (rc == LB_OK) rc = cuda_status(cudaStreamWaitEvent(lane.s, lane.done[1], 0));
+    size_t k = 0;
+    for (size_t n0 = 0; n0 < N && rc == LB_OK; n0 += C, ++k) {
       const size_t cnt = std::min(C, N - n0);
-      double* br = buf;
-      double* bu = buf + C;
-      double* bp = buf + C * (1 + d);
-      rc = cuda_status(cudaMemcpyAsync(br, rho + n0, cnt * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-      for (int k = 0; k < d && rc == LB_OK; ++k)
-        rc = cuda_status(cudaMemcpyAsync(bu + k * C, u + k * N + n0, cnt * sizeof(double), cudaMemcpyHostToDevice,
-                                         ctx->stream));
-      for (int k = 0; pineq && k < np && rc == LB_OK; ++k)
-        rc = cuda_status(cudaMemcpyAsync(bp + k * C, pineq + k * N + n0, cnt * sizeof(double),
-                                         cudaMemcpyHostToDevice, ctx->stream));
+      const int h = int(k & 1);
+      double* br = buf + size_t(h) * C * ncomp;
+      double* bu = br + C;
+      double* bp = br + C * (1 + d);
+      // the conversion of the chunk two back has left this half
+      if (k >= 2) rc = cuda_status(cudaStreamWaitEvent(lane.s, lane.done[h], 0));
+      if (rc == LB_OK)
+        rc = cuda_status(cudaMemcpyAsync(br, rho + n0, cnt * sizeof(double), cudaMemcpyHostToDevice, lane.s));
+      for (int c = 0; c < d && rc == LB_OK; ++c)
+        rc = cuda_status(cudaMemcpyAsync(bu + c * C, u + c * N + n0, cnt * sizeof(double), cudaMemcpyHostToDevice,
+                                         lane.s));
+      for (int c = 0; pineq && c < np && rc == LB_OK; ++c)
+        rc = cuda_status(cudaMemcpyAsync(bp + c * C, pineq + c * N + n0, cnt * sizeof(double),
+                                         cudaMemcpyHostToDevice, lane.s));
+      if (rc == LB_OK) rc = cuda_status(cudaEventRecord(lane.ready[h], lane.s));
+      if (rc == LB_OK) rc = cuda_status(cudaStreamWaitEvent(ctx->stream, lane.ready[h], 0));
       if (rc == LB_OK)
         rc = cuda_status(aux_init_moments_range(ctx, br, bu, pineq ? bp : nullptr, int64_t(n0), int64_t(n0 + cnt),
                                                 int64_t(C)));
+      if (rc == LB_OK) rc = cuda_status(cudaEventRecord(lane.done[h], ctx->stream));
     }
+    // nothing on the copy stream may outlive the buffer
+    if (cudaEventRecord(lane.ready[0], lane.s) == cudaSuccess) cudaStreamWaitEvent(ctx->stream, lane.ready[0], 0);
     cudaFreeAsync(buf, ctx->stream);
     if (rc == LB_OK) rc = after_state_change(ctx);
     const int rc2 = cuda_status(cudaStreamSynchronize(ctx->stream));
@@ -536,21 +579,36 @@ int lb_moments(lb_ctx* ctx, double* rho, double* u, int32_t on_device) {
     if (rc == LB_OK) rc = cuda_status(cudaStreamSynchronize(ctx->stream));
     return rc;
   }
-  // a chunk of nodes at a time through one bounded device buffer
-  const size_t C = std::max<size_t>(1, std::min(N, kChunkBytes / ((1 + d) * sizeof(double))));
+  // chunks of nodes through the two halves of one bounded device buffer:
+  // the context stream fills a half, the copy stream empties it to the host
+  const size_t C = std::max<size_t>(1, std::min(N, kChunkBytes / (2 * (1 + d) * sizeof(double))));
+  CopyLane lane;
+  LB_TRY_CUDA(lane.init());
   double* tmp = nullptr;
-  LB_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&tmp), (1 + d) * C * sizeof(double), ctx->stream));
+  LB_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&tmp), 2 * (1 + d) * C * sizeof(double), ctx->stream));
   int rc = LB_OK;
-  for (size_t n0 = 0; n0 < N && rc == LB_OK; n0 += C) {
+  size_t k = 0;
+  for (size_t n0 = 0; n0 < N && rc == LB_OK; n0 += C, ++k) {
     const size_t cnt = std::min(C, N - n0);
-    rc = cuda_status(aux_moments_range(ctx, rho ? tmp : nullptr, u ? tmp + C : nullptr, int64_t(n0),
-                                       int64_t(n0 + cnt), int64_t(C)));
+    const int h = int(k & 1);
+    double* half = tmp + size_t(h) * (1 + d) * C;
+    // the copy of the chunk two back has left this half
+    if (k >= 2) rc = cuda_status(cudaStreamWaitEvent(ctx->stream, lane.ready[h], 0));
+    if (rc == LB_OK)
+      rc = cuda_status(aux_moments_range(ctx, rho ? half : nullptr, u ? half + C : nullptr, int64_t(n0),
+                                         int64_t(n0 + cnt), int64_t(C)));
+    if (rc == LB_OK) rc = cuda_status(cudaEventRecord(lane.done[h], ctx->stream));
+    if (rc == LB_OK) rc = cuda_status(cudaStreamWaitEvent(lane.s, lane.done[h], 0));
     if (rc == LB_OK && rho)
-      rc = cuda_status(cudaMemcpyAsync(rho + n0, tmp, cnt * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    for (int k = 0; u && k < d && rc == LB_OK; ++k)
-      rc = cuda_status(cudaMemcpyAsync(u + k * N + n0, tmp + C + k * C, cnt * sizeof(double),
-                                       cudaMemcpyDeviceToHost, ctx->stream));
+      rc = cuda_status(cudaMemcpyAsync(rho + n0, half, cnt * sizeof(double), cudaMemcpyDeviceToHost, lane.s));
+    for (int c = 0; u && c < d && rc == LB_OK; ++c)
+      rc = cuda_status(cudaMemcpyAsync(u + c * N + n0, half + C + c * C, cnt * sizeof(double),
+                                       cudaMemcpyDeviceToHost, lane.s));
+    if (rc == LB_OK) rc = cuda_status(cudaEventRecord(lane.ready[h], lane.s));
   }
+  // the context stream (and so the caller's synchronisation) waits for the
+  // last copies; the buffer is freed after them
+  if (cudaEventRecord(lane.ready[0], lane.s) == cudaSuccess) cudaStreamWaitEvent(ctx->stream, lane.ready[0], 0);
   cudaFreeAsync(tmp, ctx->stream);
   const int rc2 = cuda_status(cudaStreamSynchronize(ctx->stream));
   return rc != LB_OK ? rc : rc2;
