@@ -69,8 +69,8 @@ __global__ void get_pop_kernel(Layout l, const S* __restrict__ ft, double* __res
   }
 }
 
-// f = f^eq(rho, u) + t_a (cc - cs2 I):Pi/(2 cs2^2) - t_a c.F/(2 cs2), in FP64,
-// stored shifted.  rho may be null (uniform rho_u), u may be null (uniform u_u).
+// f = f^eq(rho, u) + t_a (cc - cs2 I):Pi/(2 cs2^2) - t_a c.F/(2 cs2), stored
+// shifted.  rho may be null (uniform rho_u), u may be null (uniform u_u).
 template <class L, class S, class R>
 // nodes [n0, n1); input node idx is element idx - n0 of each component, and
 // components lie cs elements apart
@@ -101,40 +101,51 @@ __global__ void init_kernel(Layout l, S* __restrict__ ft, double rho0, const dou
         P[1][2] = P[2][1] = pineq[5 * cs + k0];
       }
     }
-    const double Fi[3] = {Fx, Fy, Fz};
-    const double drho = r - rho0;
-    double usq = 0.0, trP = 0.0;
+    // the shifted populations are computed in the kernels' arithmetic type
+    // R (FP32 for FP32 / FP16 / BF16 storage, FP64 for FP64): they are
+    // deviations of order u, so R's rounding is that of the storage; the
+    // density deviation is formed in FP64 first
+    using T = R;
+    const T drho = static_cast<T>(r - rho0);
+    const T rho0t = static_cast<T>(rho0);
+    const T Fi[3] = {static_cast<T>(Fx), static_cast<T>(Fy), static_cast<T>(Fz)};
+    T ut[3], Pt[3][3];
     for (int k = 0; k < 3; ++k) {
-      usq += ui[k] * ui[k];
-      trP += P[k][k];
+      ut[k] = static_cast<T>(ui[k]);
+      for (int m = 0; m < 3; ++m) Pt[k][m] = static_cast<T>(P[k][m]);
+    }
+    T usq = T(0), trP = T(0);
+    for (int k = 0; k < 3; ++k) {
+      usq += ut[k] * ut[k];
+      trP += Pt[k][k];
     }
     // f_a = t_a [drho + rho0 (3 c.u + 4.5 (c.u)^2 - 1.5 u.u) + 4.5 (c.P.c - tr P / 3)
     //           - 1.5 c.F]: a velocity pair {a, abar} shares the even part
     // and takes the odd part (c.u, c.F) with opposite signs
-    const double ev0 = drho - 1.5 * rho0 * usq - 1.5 * trP;
-    ft[0 * l.vol + o] = store_as<S, R>(static_cast<R>(weight<L>(0) * ev0));
+    const T ev0 = drho - T(1.5) * rho0t * usq - T(1.5) * trP;
+    ft[0 * l.vol + o] = store_as<S, R>(static_cast<R>(T(weight<L>(0)) * ev0));
     static_for<0, n_pairs<L>()>([&](auto P_) {
       constexpr int a = pair_first<L>(decltype(P_)::value);
       constexpr int b = L::opp(a);
       // c.u, c.F and c.P.c with the components of c (0 or +-1) applied at
       // compile time
-      double cu = 0.0, cF = 0.0, cPc = 0.0;
+      T cu = T(0), cF = T(0), cPc = T(0);
       static_for<0, 3>([&](auto I_) {
         constexpr int i = decltype(I_)::value;
         constexpr int ci = comp<L>(i, a);
         if constexpr (ci != 0) {
-          cu += ci > 0 ? ui[i] : -ui[i];
+          cu += ci > 0 ? ut[i] : -ut[i];
           cF += ci > 0 ? Fi[i] : -Fi[i];
         }
         static_for<0, 3>([&](auto J_) {
           constexpr int j = decltype(J_)::value;
           constexpr int cc = ci * comp<L>(j, a);
-          if constexpr (cc != 0) cPc += cc > 0 ? P[i][j] : -P[i][j];
+          if constexpr (cc != 0) cPc += cc > 0 ? Pt[i][j] : -Pt[i][j];
         });
       });
-      const double w = weight<L>(a);
-      const double even = w * (ev0 + 4.5 * (rho0 * cu * cu + cPc));
-      const double odd = w * (3.0 * rho0 * cu - 1.5 * cF);
+      const T w = T(weight<L>(a));
+      const T even = w * (ev0 + T(4.5) * (rho0t * cu * cu + cPc));
+      const T odd = w * (T(3) * rho0t * cu - T(1.5) * cF);
       ft[a * l.vol + o] = store_as<S, R>(static_cast<R>(even + odd));
       ft[b * l.vol + o] = store_as<S, R>(static_cast<R>(even - odd));
     });
