@@ -127,9 +127,11 @@ LB_API int lb_create(int32_t lattice, const int64_t dims[3], double tau, const l
 /* Sets the state to f = f^eq(rho, u) + fhat^neq(pineq) - t_a c_a.F/(2 cs2):
  * Eq. equil plus the order-2 Hermite non-equilibrium part, shifted so that
  * the state reports u.  rho [N], u [d][N], pineq [3 or 6][N] or NULL (= 0).
- * All three are host (on_device = 0) or device (on_device = 1) FP64 arrays.
- * Host arrays cross a chunk of nodes at a time through one device buffer of
- * at most 512 MB (pinned host memory moves at the copy engines' rate). */
+ * All three are host (on_device = 0) or device (on_device = 1) FP64 arrays;
+ * the stored (shifted) populations are computed in the kernels' arithmetic
+ * (FP64 for LB_F64 storage, FP32 otherwise).  Host arrays cross a chunk of
+ * nodes at a time through one device buffer of at most 512 MB, the copies
+ * overlapping the conversion. */
 LB_API int lb_init_moments(lb_ctx* ctx, const double* rho, const double* u, const double* pineq,
                     int32_t on_device);
 
