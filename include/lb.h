@@ -191,6 +191,25 @@ typedef struct {
 } lb_memory_plan_t;
 LB_API int lb_memory_plan(int32_t lattice, int32_t bytes_per_value, lb_memory_plan_t* out);
 
+/* The brick decomposition that lb_create() would choose for the fused scheme
+ * (no device is touched): brick bx x by x bz columns and their counts, the
+ * TMA pipeline depth, nodes per thread, dedicated export warps, dynamic
+ * shared memory per CTA and the shell size (elements of one parity: every
+ * brick face keeps the outgoing populations of its boundary nodes).  tile as
+ * lb_options.tile (NULL = default); sms > 0 plans the sweep length for that
+ * many SMs (0 = the current device's count, 152 if none is visible).  dims
+ * in user axes as for lb_create().  Errors: LB_E_INVAL, LB_E_UNSUPPORTED (no
+ * compiled brick shape matches the request). */
+typedef struct {
+  int32_t bx, by, bz, nbx, nby, nbz;
+  int64_t bricks;
+  int32_t tma_slots, nodes_per_thread, export_warps;
+  int64_t shared_bytes;
+  int64_t shell_elems_per_parity;
+} lb_plan_t;
+LB_API int lb_plan_fused(int32_t lattice, int32_t storage, const int64_t dims[3], const int32_t tile[3],
+                         int32_t sms, lb_plan_t* out);
+
 /* Allocation-free step for callers that cannot let a library call
  * cudaMalloc (device memory owned by another allocator or a fixed budget, or
  * loops that must not enter the driver's allocator).  The paper has no

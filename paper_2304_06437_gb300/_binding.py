@@ -92,6 +92,14 @@ class lb_tune_entry(ctypes.Structure):
     ]
 
 
+class lb_plan_t(ctypes.Structure):
+    _fields_ = [("bx", ctypes.c_int32), ("by", ctypes.c_int32), ("bz", ctypes.c_int32),
+                ("nbx", ctypes.c_int32), ("nby", ctypes.c_int32), ("nbz", ctypes.c_int32),
+                ("bricks", ctypes.c_int64), ("tma_slots", ctypes.c_int32), ("nodes_per_thread", ctypes.c_int32),
+                ("export_warps", ctypes.c_int32), ("shared_bytes", ctypes.c_int64),
+                ("shell_elems_per_parity", ctypes.c_int64)]
+
+
 class lb_batch_info_t(ctypes.Structure):
     _fields_ = [
         ("n_domains", ctypes.c_int32),
@@ -150,6 +158,8 @@ SIGNATURES = {
     "lb_cg_sync": (ctypes.c_int, [_vp]),
     "lb_cg_destroy": (None, [_vp]),
     "lb_cg_set_nci": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int32]),
+    "lb_plan_fused": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _i64p, _P(ctypes.c_int32), ctypes.c_int32,
+                                     _P(lb_plan_t)]),
     "lb_selftest_timeout": (ctypes.c_int, [ctypes.c_int64, _i64p]),
     "lb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lb_abi_version": (ctypes.c_int, []),

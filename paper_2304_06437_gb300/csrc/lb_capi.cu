@@ -268,6 +268,40 @@ int lb_memory_plan(int32_t lattice, int32_t bytes_per_value, lb_memory_plan_t* o
   return LB_OK;
 }
 
+int lb_plan_fused(int32_t lattice, int32_t storage, const int64_t dims[3], const int32_t tile[3], int32_t sms,
+                  lb_plan_t* out) {
+  if (!out || !dims || sms < 0) return LB_E_INVAL;
+  const int q = lattice_q(lattice);
+  if (q < 0 || storage_bytes(storage) == 0) return LB_E_INVAL;
+  const int d = lattice_d(lattice);
+  for (int k = 0; k < 3; ++k)
+    if (dims[k] < 1 || dims[k] > (int64_t(1) << 30)) return LB_E_INVAL;
+  if (d == 2 && dims[2] != 1) return LB_E_INVAL;
+  // the internal axes of lb_create: 2D (x, y) -> (x, z)
+  Geometry g{};
+  g.lattice = lattice;
+  g.q = q;
+  g.d = d;
+  g.nx = int(dims[0]);
+  g.ny = d == 2 ? 1 : int(dims[1]);
+  g.nz = d == 2 ? int(dims[1]) : int(dims[2]);
+  FusedPlan p{};
+  if (!k1_plan(g, storage, tile, &p, sms)) return LB_E_UNSUPPORTED;
+  out->bx = p.bx;
+  out->by = p.by;
+  out->bz = p.bz;
+  out->nbx = p.nbx;
+  out->nby = p.nby;
+  out->nbz = p.nbz;
+  out->bricks = int64_t(p.nbx) * p.nby * p.nbz;
+  out->tma_slots = p.slots;
+  out->nodes_per_thread = p.npt;
+  out->export_warps = p.xwarps;
+  out->shared_bytes = int64_t(p.smem_bytes);
+  out->shell_elems_per_parity = p.sx_elems + p.sy_elems + p.sz_elems;
+  return LB_OK;
+}
+
 int lb_create(int32_t lattice, const int64_t dims[3], double tau, const lb_boundary* bnd, const lb_options* opt_in,
               lb_ctx** out) {
   if (!out) return LB_E_INVAL;

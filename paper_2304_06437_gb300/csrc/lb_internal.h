@@ -80,7 +80,8 @@ size_t k0_aux_bytes(const Geometry& g, int storage);
 cudaError_t k0_step_buffers(const Geometry& g, double* ft, double* mom, cudaStream_t stream);
 
 // ---- fused scheme (lb_k1_*.cu)
-bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPlan* plan);
+// sms > 0 plans for that many SMs instead of the current device's count
+bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPlan* plan, int sms = 0);
 // plan with one given compiled shape (a K1Variant*, see lb_k1_launch.cuh) and
 // sweep length bz (0 = the planner's choice)
 bool k1_plan_variant(const Geometry& g, const void* variant, int bz, FusedPlan* plan);

@@ -110,7 +110,7 @@ static int choose_bz(int nz, int columns, int slots, int sms) {
   return best_bz;
 }
 
-static void fill_plan(const Geometry& g, const K1Variant* v, int req_bz, FusedPlan* plan) {
+static void fill_plan(const Geometry& g, const K1Variant* v, int req_bz, FusedPlan* plan, int sms = 0) {
   FusedPlan p{};
   p.bx = v->bx;
   p.by = v->by;
@@ -123,7 +123,7 @@ static void fill_plan(const Geometry& g, const K1Variant* v, int req_bz, FusedPl
   p.nbx = (g.nx + p.bx - 1) / p.bx;
   p.nby = (g.ny + p.by - 1) / p.by;
   const int columns = p.nbx * p.nby;
-  p.bz = req_bz > 0 ? (req_bz < g.nz ? req_bz : g.nz) : choose_bz(g.nz, columns, p.slots, sm_count());
+  p.bz = req_bz > 0 ? (req_bz < g.nz ? req_bz : g.nz) : choose_bz(g.nz, columns, p.slots, sms > 0 ? sms : sm_count());
   p.nbz = (g.nz + p.bz - 1) / p.bz;
   int nxf = 0, nyf = 0, nzf = 0;
   dispatch_lattice(g.lattice, [&](auto Lt) {
@@ -142,14 +142,14 @@ static void fill_plan(const Geometry& g, const K1Variant* v, int req_bz, FusedPl
   *plan = p;
 }
 
-bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPlan* plan) {
+bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPlan* plan, int sms) {
   const int rbx = tile_req ? tile_req[0] : 0;
   const int rby = tile_req ? tile_req[1] : 0;
   int rns, rwb, rnxw, rnpt, rts;
   pipeline_request(&rns, &rwb, &rnxw, &rnpt, &rts);
   const K1Variant* v = find_variant(g.lattice, storage, rbx, rby, rns, rwb, rnxw, rnpt, rts);
   if (!v) return false;
-  fill_plan(g, v, tile_req ? tile_req[2] : 0, plan);
+  fill_plan(g, v, tile_req ? tile_req[2] : 0, plan, sms);
   return true;
 }
 

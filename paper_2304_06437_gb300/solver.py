@@ -326,6 +326,20 @@ def lattice_table(lattice):
     return c, w, opp
 
 
+def fused_plan(lattice, dims, storage="f32", tile=None, sms=0) -> dict:
+    """The brick decomposition lb_create() would choose (lb_plan_fused; no
+    device is touched)."""
+    lib = B.load()
+    lid = B.LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+    st = B.STORAGES[storage] if isinstance(storage, str) else int(storage)
+    dims = list(dims) + [1] * (3 - len(dims))
+    t = (ctypes.c_int32 * 3)(*tile) if tile is not None else None
+    p = B.lb_plan_t()
+    B.check(lib.lb_plan_fused(lid, st, (ctypes.c_int64 * 3)(*[int(v) for v in dims[:3]]), t, int(sms),
+                              ctypes.byref(p)), "lb_plan_fused")
+    return {name: getattr(p, name) for name, _ in p._fields_}
+
+
 def memory_plan(lattice, bytes_per_value=4) -> dict:
     lib = B.load()
     lid = B.LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
