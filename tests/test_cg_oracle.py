@@ -134,15 +134,18 @@ def _profile_field(ny=6):
     # x = 18 -> {16, 0} (periodic); x = 17 and 19 see a bulk node at distance 2.
     (2, [0, 3, 7, 8, 9, 12, 13, 16]),
 ])
-def test_nci_flags_hand_worked_film_profile(h, expected):
+@pytest.mark.parametrize("lat", ["D2Q9", "D3Q19"])
+def test_nci_flags_hand_worked_film_profile(h, expected, lat):
     """The flags of the section 2.2 test on a profile whose answer is worked
     out by hand: a bulk node (phi < -1 + eps) with non-bulk points at distance
     h along a pair of opposite directions flags those two points.  Diagonal
-    directions give the same columns in a y-uniform field; the y direction
-    none."""
-    phi, nx, ny = _profile_field()
-    cfg = oracle.make_cg_cfg("D2Q9", (nx, ny), 0.8, 0.01, 0.7, nci_amp=1e-3, nci_eps=0.1, nci_h=h)
-    fl = oracle.cg_nci_flags(cfg, phi).reshape(ny, nx)
+    directions give the same columns in a field uniform across x; the
+    directions without an x component none (D2Q9: 6 rows; D3Q19: 5 x 4
+    cross-sections)."""
+    phi, nx, ny = _profile_field(6 if lat == "D2Q9" else 20)
+    dims = (nx, ny) if lat == "D2Q9" else (nx, 5, 4)
+    cfg = oracle.make_cg_cfg(lat, dims, 0.8, 0.01, 0.7, nci_amp=1e-3, nci_eps=0.1, nci_h=h)
+    fl = oracle.cg_nci_flags(cfg, phi).reshape(-1, nx)
     assert (fl == fl[0]).all()
     assert list(np.nonzero(fl[0])[0]) == expected
 
