@@ -227,11 +227,16 @@ LB_API int lb_plan_fused(int32_t lattice, int32_t storage, const int64_t dims[3]
  * of LB_NOALLOC_SCRATCH_BYTES, shared by every call on a device and kept
  * until the process exits.  Hence (1 + d + d(d+1)/2) * N * 8 bytes must fit:
  * N <= 1,398,101 nodes for D2Q9 and N <= 838,860 for D3Q19 / D3Q27; larger
- * grids return LB_E_TOO_LARGE before any GPU work.  The first call on a
- * device looks up the array's device address (make it before any stream
- * capture).  Calls that overlap on the GPU race on the shared array: order
- * them on one stream.  Errors: LB_E_INVAL, LB_E_TOO_LARGE, LB_E_UNSUPPORTED
- * (internal y or z extent above 65535), LB_E_CUDA. */
+ * grids return LB_E_TOO_LARGE before any GPU work.  The first call in a
+ * CUDA context (normally the device's primary context) looks up the array's
+ * device address in that context and caches it under the context's unique id
+ * (make that call before any stream capture); a new context, for instance
+ * after cudaDeviceReset(), gets its own look-up.  Calls that overlap on the
+ * GPU race on the shared array: order them on one stream.  Errors:
+ * LB_E_INVAL, LB_E_TOO_LARGE, LB_E_UNSUPPORTED (internal y or z extent above
+ * 65535): f untouched.  LB_E_CUDA: if a step's launch failed, f is shifted
+ * back and holds the populations after an unspecified number of completed
+ * steps; after a sticky device error its contents are undefined. */
 #define LB_NOALLOC_SCRATCH_BYTES (64ull << 20)
 LB_API int lb_step_noalloc(int32_t lattice, const int64_t dims[3], double tau, const lb_boundary* bnd,
                            double rho0, const double force[3], double* f, int64_t n, void* stream);

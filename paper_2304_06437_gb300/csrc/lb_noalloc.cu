@@ -15,13 +15,18 @@
 //    otherwise from library load), that device keeps the array until the
 //    process exits;
 //  * host code never passes the array's name to a kernel (on the host it is
-//    only a stand-in symbol): the first call on each device, with that device
-//    current, looks up its device address with cudaGetSymbolAddress and caches
-//    it, so make that first call before any stream capture;
+//    only a stand-in symbol): the first call in each CUDA context (normally
+//    the device's primary context), with that context current, looks up its
+//    device address with cudaGetSymbolAddress and caches it under the
+//    context's unique id, so make that first call before any stream capture;
+//    a context created later (after cudaDeviceReset, or a driver-API context
+//    made current by the caller) has a new id and gets its own look-up, never
+//    a stale address;
 //  * every call on a device shares the same array and leaves its last
 //    contents behind; the moments kernel overwrites every entry it later
 //    reads, so nothing needs clearing, but calls that overlap on the GPU
 //    (different streams, no ordering) race on the array.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -32,27 +37,73 @@
 namespace {
 
 constexpr size_t kScratchDoubles = LB_NOALLOC_SCRATCH_BYTES / sizeof(double);
-constexpr int kMaxDevices = 64;
+constexpr int kCacheEntries = 64;
 
 static __device__ __align__(256) double g_lb_noalloc_scratch[kScratchDoubles];
 
 std::mutex g_setup_mutex;
-double* g_scratch_addr[kMaxDevices] = {nullptr};
 
-// device address of the scratch array on the current device (set-up once)
-cudaError_t scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+// cache of the array's device address per CUDA context, keyed by the
+// context's process-unique id (cuCtxGetId; a handle value can be reused after
+// a context is destroyed, an id cannot)
+struct ScratchEntry {
+  unsigned long long ctx_id;
+  double* addr;
+};
+ScratchEntry g_scratch_cache[kCacheEntries] = {};
+int g_scratch_used = 0, g_scratch_next = 0;
+
+typedef CUresult (*PFN_ctx_get_current)(CUcontext*);
+typedef CUresult (*PFN_ctx_get_id)(CUcontext, unsigned long long*);
+
+template <class F>
+cudaError_t driver_fn(const char* name, unsigned version, F* out) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion(name, &fn, version, cudaEnableDefault, &q);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorSymbolNotFound;
+  *out = reinterpret_cast<F>(fn);
+  return cudaSuccess;
+}
+
+// device address of the scratch array in the current context (set-up once per
+// context)
+cudaError_t scratch_address(double** out) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
+  static PFN_ctx_get_current get_current = nullptr;
+  static PFN_ctx_get_id get_id = nullptr;
+  cudaError_t e;
+  if (!get_current && (e = driver_fn("cuCtxGetCurrent", 4000, &get_current)) != cudaSuccess) return e;
+  if (!get_id && (e = driver_fn("cuCtxGetId", 12000, &get_id)) != cudaSuccess) return e;
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  void* p = nullptr;
+  if (!ctx) {
+    // no context current yet: the runtime call below makes the device's
+    // primary context current
     e = cudaGetSymbolAddress(&p, g_lb_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<double*>(p);
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
   }
-  *out = g_scratch_addr[dev];
+  unsigned long long id = 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  for (int k = 0; k < g_scratch_used; ++k)
+    if (g_scratch_cache[k].ctx_id == id) {
+      *out = g_scratch_cache[k].addr;
+      return cudaSuccess;
+    }
+  if (!p) {
+    e = cudaGetSymbolAddress(&p, g_lb_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+  }
+  // a full table recycles its oldest entry: that context only looks its
+  // address up again on its next call
+  ScratchEntry& slot = g_scratch_cache[g_scratch_used < kCacheEntries ? g_scratch_used++ : g_scratch_next];
+  if (g_scratch_used == kCacheEntries) g_scratch_next = (g_scratch_next + 1) % kCacheEntries;
+  slot.ctx_id = id;
+  slot.addr = static_cast<double*>(p);
+  *out = slot.addr;
   return cudaSuccess;
 }
 
@@ -140,13 +191,14 @@ extern "C" int lb_step_noalloc(int32_t lattice, const int64_t dims[3], double ta
     shift_kernel<L><<<int(blocks), 256, 0, st>>>(f, N, rho0, 1);
   });
   e = cudaGetLastError();
+  if (e != cudaSuccess) return status_of(e);
   for (int64_t i = 0; i < n && e == cudaSuccess; ++i) e = k0_step_buffers(g, f, mom, st);
-  if (e == cudaSuccess) {
-    dispatch_lattice(lattice, [&](auto Lt) {
-      using L = decltype(Lt);
-      shift_kernel<L><<<int(blocks), 256, 0, st>>>(f, N, rho0, 0);
-    });
-    e = cudaGetLastError();
-  }
-  return status_of(e);
+  // shift back even when a step failed to launch, so that f holds unshifted
+  // populations after however many steps did complete
+  dispatch_lattice(lattice, [&](auto Lt) {
+    using L = decltype(Lt);
+    shift_kernel<L><<<int(blocks), 256, 0, st>>>(f, N, rho0, 0);
+  });
+  const cudaError_t e2 = cudaGetLastError();
+  return status_of(e != cudaSuccess ? e : e2);
 }

@@ -34,6 +34,7 @@ from typing import Callable, List, Optional
 
 import numpy as np
 
+from ._binding import LB_E_NOMEM, LBError
 from .solver import Batch, Solver
 
 
@@ -129,9 +130,18 @@ class Server:
             if (self.active and self.max_active_nodes is not None and
                     sum(s.n for _, s in self.active) + int(np.prod(req.dims)) > self.max_active_nodes):
                 break
+            try:
+                s = Solver(req.lattice, req.dims, req.tau, faces=req.faces, wall_u=req.wall_u, force=req.force,
+                           storage=req.storage, stream=self.stream)
+            except LBError as e:
+                # the footprint estimate fell short, or another process took
+                # the memory since it was read: keep the request queued and
+                # retry once a resident domain retires (an empty server has
+                # nothing to wait for, so there the error stands)
+                if e.code != LB_E_NOMEM or not self.active:
+                    raise
+                break
             self.queue.pop(pick)
-            s = Solver(req.lattice, req.dims, req.tau, faces=req.faces, wall_u=req.wall_u, force=req.force,
-                       storage=req.storage, stream=self.stream)
             s.reduce(residual=True)  # residual baseline: u at admission
             req.admitted = self.clock()
             self.active.append((req, s))

@@ -12,6 +12,7 @@ import pytest
 import oracle
 import synth
 from lbcase import dim_of, faces_for, oracle_cfg, random_state, rel_l2
+from oracle.storage import round_populations
 
 pytestmark = pytest.mark.gpu
 
@@ -201,6 +202,82 @@ def test_conservation_and_reductions(Solver, lat):
     assert np.abs(np.array(r1["momentum"]) - np.array(r0["momentum"])).max() < 1e-13 * rho.size
     assert abs(r0["mass"] - rho.sum()) < 1e-9
     assert r1["residual"] == 1.0
+
+
+def _numpy_reductions(lat, cfg, f, f_prev, force, rho0=1.0):
+    """Mass, momentum and the relative velocity residual of oracle states,
+    summed with numpy from their definitions (section 2's moments; u =
+    (j + F/2)/rho0).  Returns the residual against the exact previous
+    velocity and against that velocity rounded to FP32 (the snapshot the
+    library keeps)."""
+    c = oracle.lattice_tables(lat)[0]
+    d = dim_of(lat)
+    F = np.asarray(force, float)[:d]
+
+    def vel(g):
+        return (c[:, :d].T @ g + 0.5 * F[:, None]) / rho0
+
+    u, up = vel(f), vel(f_prev)
+    up32 = up.astype(np.float32).astype(np.float64)
+    nu = np.linalg.norm(u)
+    return {"mass": f.sum(), "momentum": c[:, :d].T @ f.sum(axis=1),
+            "residual": np.linalg.norm(u - up) / nu, "residual_f32prev": np.linalg.norm(u - up32) / nu,
+            "unorm": nu, "upnorm": np.linalg.norm(up)}
+
+
+@pytest.mark.parametrize("lat", LATTICES)
+@pytest.mark.parametrize("case", ["periodic_forced_flow", "lid"])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_reductions_match_numpy_sums_of_oracle_states(Solver, lat, case, storage):
+    """lb_reduce (S6) against numpy sums over two oracle states t and t + K:
+    a mean flow (or a driven lid) makes the momentum non-zero and changing,
+    so a wrong or constant value fails; the residual is compared with the
+    definition ||u_t+K - u_t|| / ||u_t+K||."""
+    d = dim_of(lat)
+    dims = (40, 28, 1) if d == 2 else (17, 13, 11)
+    if case == "lid":
+        faces, wall_u = faces_for(lat, "lid")
+        force = (0.0, 0.0, 0.0)
+    else:
+        faces, wall_u = [0] * 6, None
+        force = (3e-5, -2e-5, 1e-5)[:d] + (0.0,) * (3 - d)
+    cfg = oracle_cfg(lat, dims, 0.62, faces, wall_u, force=force)
+    rho, u, pineq = synth.smooth_random_state(dims, d, seed=17)
+    u = u + np.array([0.02, -0.013, 0.007][:d])[:, None]
+    f_a = oracle.run(cfg, oracle.init(cfg, rho, np.ascontiguousarray(u), pineq), 5)
+    f_b = oracle.run(cfg, f_a, 20)
+    # the states as stored (FP32 storage rounds each shifted population): the
+    # reductions read the stored values, so the numpy sums take the same ones
+    w = oracle.lattice_tables(lat)[1]
+    f_a = round_populations(f_a, w, storage)
+    f_b = round_populations(f_b, w, storage)
+    s = Solver(lat, dims, 0.62, faces=faces, wall_u=wall_u, storage=storage, force=force)
+    s.set_populations(np.ascontiguousarray(f_a))
+    first = s.reduce(residual=True)
+    s.set_populations(np.ascontiguousarray(f_b))
+    got = s.reduce(residual=True)
+    s.close()
+    want_a = _numpy_reductions(lat, cfg, f_a, f_a, force)
+    want = _numpy_reductions(lat, cfg, f_b, f_a, force)
+    # the first residual has no previous velocity: 1 by definition
+    assert first["residual"] == 1.0
+    # FP64 sums of the same stored values: rounding order only
+    tol = 1e-13
+    assert abs(first["mass"] - want_a["mass"]) <= tol * want_a["mass"]
+    assert abs(got["mass"] - want["mass"]) <= tol * want["mass"]
+    mom_scale = np.abs(want["momentum"]).max()
+    assert mom_scale > 1e-3 * f_b.shape[1]  # the momentum is far from zero
+    assert np.abs(np.array(got["momentum"]) - want["momentum"]).max() <= tol * mom_scale
+    assert np.abs(np.array(first["momentum"]) - want_a["momentum"]).max() <= tol * mom_scale
+    assert np.abs(want["momentum"] - want_a["momentum"]).max() > 1e-6 * mom_scale  # it changed over K steps
+    # the residual: against the FP32-snapshot definition tightly, and against
+    # the exact definition within the snapshot's rounding bound
+    # | ||u - fl(up)|| - ||u - up|| | <= ||fl(up) - up|| <= 2^-24 ||up||
+    r = got["residual"]
+    assert want["residual"] > 1e-4
+    rtol = 1e-10
+    assert abs(r - want["residual_f32prev"]) <= rtol * want["residual"]
+    assert abs(r - want["residual"]) <= 2.0 ** -24 * want["upnorm"] / want["unorm"] + rtol * want["residual"]
 
 
 def test_init_moments_device_buffers_and_readback(Solver):

@@ -119,3 +119,41 @@ def test_poisson_stream_is_seeded_and_in_range():
     assert all(32 <= x.dims[0] <= 256 for x in a)
     assert all(x.tau >= 0.51 for x in a)
     assert np.all(np.diff([x.arrival for x in a]) > 0)
+
+
+def test_allocation_failure_keeps_the_request_queued(fake, monkeypatch):
+    """A request whose allocation fails while others are resident stays in
+    the queue and is admitted after a resident domain retires."""
+    from paper_2304_06437_gb300 import _binding as B
+
+    class FailingOnce(FakeSolver):
+        failed = False
+
+        def __init__(self, lattice, dims, *a, **k):
+            if dims[0] == 30 and not FailingOnce.failed:
+                FailingOnce.failed = True
+                raise B.LBError(B.LB_E_NOMEM, "lb_create")
+            super().__init__(lattice, dims, *a, **k)
+
+    monkeypatch.setattr(serve, "Solver", FailingOnce)
+    srv = fake.Server(round_steps=100, clock=Clock(0.01), free_bytes=lambda: 1 << 40, reserve_bytes=0)
+    srv.submit(_req(0, 0.0, 10))
+    srv.submit(_req(1, 0.0, 30))
+    srv.step_round()
+    assert [r.rid for r, _ in srv.active] == [0] and [r.rid for r in srv.queue] == [1]
+    done = srv.run()
+    assert sorted(r.rid for r in done) == [0, 1] and all(r.converged for r in done)
+    assert FakeSolver.live == 0
+
+
+def test_allocation_failure_on_an_empty_server_is_raised(fake, monkeypatch):
+    from paper_2304_06437_gb300 import _binding as B
+
+    def failing(*a, **k):
+        raise B.LBError(B.LB_E_NOMEM, "lb_create")
+
+    monkeypatch.setattr(serve, "Solver", failing)
+    srv = fake.Server(round_steps=100, clock=Clock(0.01), free_bytes=lambda: 1 << 40, reserve_bytes=0)
+    srv.submit(_req(0, 0.0, 10))
+    with pytest.raises(B.LBError):
+        srv.step_round()
