@@ -40,6 +40,8 @@ WORKLOADS = {
     "cavity_d3q19_256": dict(lattice="D3Q19", dims=(256, 256, 256), tau=0.52, flow="cavity", lid=0.05),
     # profiling case: 2.5 GB, yet every brick sweeps 512 planes as at 1024^3
     "cavity_d3q19_256x512": dict(lattice="D3Q19", dims=(256, 256, 512), tau=0.52, flow="cavity", lid=0.05),
+    # the D3Q27 Taylor-Green vortex at 1.07e9 nodes (one FP32 array, 116 GB)
+    "tg_d3q27_1024": dict(lattice="D3Q27", dims=(1024, 1024, 1024), tau=0.8, flow="tg3d", u0=0.02),
     "tg_d3q27_512": dict(lattice="D3Q27", dims=(512, 512, 512), tau=0.8, flow="tg3d", u0=0.02),
     "tg_d3q27_256": dict(lattice="D3Q27", dims=(256, 256, 256), tau=0.8, flow="tg3d", u0=0.02),
     "tg_d2q9_16384": dict(lattice="D2Q9", dims=(16384, 16384, 1), tau=0.8, flow="tg2d", u0=0.01),
@@ -227,50 +229,26 @@ def init_state(solver, w, torch):
     torch.cuda.empty_cache()
 
 
-def cpu_oracle_rate(lattice, budget_s=12.0, n=80, tau=0.52, lid=0.05, threads=0):
-    """The FP64 CPU oracle on a bounded sample of the workload (cavity cube of side n)."""
-    import oracle
-    import synth
-    faces = [1, 1, 1, 2, 1, 1]
-    wall_u = [[0, 0, 0]] * 3 + [[lid, 0, 0]] + [[0, 0, 0]] * 2
-    dims = (n, n, n) if lattice != "D2Q9" else (n * 8, n * 8, 1)
-    if lattice == "D2Q9":
-        faces = faces[:4] + [0, 0]
-    cfg = oracle.make_cfg(lattice, dims, tau, faces=faces, wall_u=wall_u)
-    rho, u = synth.rest_state(dims, 2 if lattice == "D2Q9" else 3)
-    f = oracle.init(cfg, rho, u)
-    N = dims[0] * dims[1] * dims[2]
-    f = oracle.run(cfg, f, 1, threads)  # warm
-    steps = 0
-    t0 = time.perf_counter()
-    while True:
-        f = oracle.run(cfg, f, 1, threads)
-        steps += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt = time.perf_counter() - t0
-    used = threads if threads > 0 else oracle.max_threads()
-    return N * steps / dt / 1e6, used, "%s lid-driven cavity %s, %d steps from rest (FP64 oracle, two arrays)" % (
-        lattice, "x".join(map(str, dims)), steps)
-
-
 def run_reference(args, w):
-    """--impl reference: the CPU oracle, timed on a bounded sample of the workload."""
+    """--impl reference: the CPU oracle, timed on a bounded sample of the
+    workload (the sample of the default run's cpu_baseline: the workload's
+    flow at its parity size)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle
-    import synth
     lattice = w["lattice"]
-    n = 80  # the sample of the default run's cpu_baseline
-    dims = (n, n, n) if lattice != "D2Q9" else (1024, 1024, 1)
-    faces, wall_u = boundary(w)
+    dims, _ = PARITY_SIZE[w["flow"]]
+    wsz = dict(w)
+    wsz["dims"] = dims
+    if w["flow"] == "channel":
+        wsz["force"] = 1e-6
+    faces, wall_u = boundary(wsz)
     if lattice == "D2Q9":
         faces = faces[:4] + [0, 0]
-    cfg = oracle.make_cfg(lattice, dims, w["tau"], faces=faces, wall_u=wall_u)
-    d = 2 if lattice == "D2Q9" else 3
-    rho, u = synth.rest_state(dims, d)
-    f = oracle.init(cfg, rho, u)
+    cfg = oracle.make_cfg(lattice, dims, w["tau"], force=force_of(wsz), faces=faces, wall_u=wall_u)
+    rho, u, pineq = parity_fields(wsz, dims)
+    f = oracle.init(cfg, rho, u, pineq)
     f = oracle.run(cfg, f, args.warmup)
     t0 = time.perf_counter()
     f = oracle.run(cfg, f, args.steps)
@@ -278,8 +256,8 @@ def run_reference(args, w):
     N = dims[0] * dims[1] * dims[2]
     value = N * args.steps / dt / 1e6
     cores = oracle.max_threads()
-    sample = "%s %s, %d timed steps (FP64 CPU oracle, two arrays, OpenMP)" % (lattice, "x".join(map(str, dims)),
-                                                                          args.steps)
+    sample = "%s %s %s, %d timed steps (FP64 CPU oracle, two arrays, OpenMP)" % (
+        lattice, w["flow"], "x".join(map(str, dims)), args.steps)
     line = {
         "impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
@@ -382,13 +360,10 @@ def main():
         "algorithmic_bytes_per_update": 2 * q * es,
     }
 
-    # ---- accuracy: the timed run against the analytic profile (channel), and
-    # the same storage at a parity size against the FP64 path of the library
+    # ---- accuracy of the timed run against the analytic profile (channel)
     accuracy = {}
     if w["flow"] == "channel":
         accuracy["u_vs_parabola_after_timed_steps"] = channel_error(s, w, torch)
-    if not args.no_accuracy:
-        accuracy.update(side_accuracy(w, args, torch))
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -396,10 +371,13 @@ def main():
         e2e = measure_e2e(s, w, args, torch, stream)
 
     s.close()
+    # ---- CPU baseline (the FP64 oracle on a bounded sample) and, from the
+    # same oracle run, the error of the benchmark's storage at a parity size
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, cores, sample = cpu_oracle_rate(lattice)
-        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample}
+        cpu, ref = cpu_baseline_leg(w)
+        if not args.no_accuracy:
+            accuracy.update(side_accuracy(w, args, torch, ref))
 
     if rank == 0:
         line = {
@@ -715,34 +693,104 @@ PARITY_SIZE = {"cavity": ((64, 64, 64), 200), "tg3d": ((64, 64, 64), 200), "tg2d
                "channel": ((64, 64, 64), 2000)}
 
 
-def side_accuracy(w, args, torch):
-    """The benchmark's storage and scheme against the library's FP64 path (the
-    path the tests hold to 1e-12 of the CPU oracle) on the same flow at a
-    parity size: relative L2 of rho and u."""
-    from paper_2304_06437_gb300 import Solver
+def parity_fields(w, dims):
+    """Initial (rho, u, pineq) of the workload's flow at a parity size, as
+    host arrays (the same seeded/analytic fields feed the oracle and the GPU)."""
+    import synth
+    d = 2 if w["lattice"] == "D2Q9" else 3
+    if w["flow"] == "cavity":
+        rho, u = synth.rest_state(dims, d)
+        return rho, u, None
+    if w["flow"] == "channel":
+        rho, u = synth.channel_state(dims, 1e-6, 1.0, (w["tau"] - 0.5) / 3.0, d)
+        return rho, u, None
+    if w["flow"] == "tg3d":
+        return synth.taylor_green_3d(dims[0], w["u0"], 1.0, w["tau"])
+    return synth.taylor_green_2d(dims[0], w["u0"], 1.0, w["tau"])
+
+
+def cpu_baseline_leg(w, budget_s=12.0, threads=0):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    the workload's flow at its parity size (cavity and Taylor-Green 64^3 x 200
+    steps, 2D Taylor-Green 256^2 x 1000, channel from the parabola 2000
+    steps), timed on the host cores.  Its final rho and u are also the FP64
+    reference of the benchmark's accuracy field.  If the parity run takes less
+    than the budget, the sample continues from its end state until the budget
+    is spent, and the rate covers every timed step.  (The channel flow is
+    uniform in x and z, so its reference runs on a 1 x 64 x 1 column, whose
+    fields equal every column of the 64^3 box; the timing runs the 64^3 box.)"""
+    import oracle
     dims, steps = PARITY_SIZE[w["flow"]]
     ws = dict(w)
     ws["dims"] = dims
     if w["flow"] == "channel":
         ws["force"] = 1e-6  # the H = 64 force of the channel study
     faces, wall_u = boundary(ws)
-    out = {}
-    for storage in ("f64", args.storage):
-        s = Solver(w["lattice"], dims, w["tau"], faces=faces, wall_u=wall_u, storage=storage,
-                   scheme=args.scheme, force=force_of(ws))
-        init_state(s, ws, torch)
-        s.step(steps)
-        N = dims[0] * dims[1] * dims[2]
-        d = 2 if w["lattice"] == "D2Q9" else 3
-        rho = torch.empty(N, device="cuda", dtype=torch.float64)
-        u = torch.empty((d, N), device="cuda", dtype=torch.float64)
-        s.moments(rho, u)
-        s.close()
-        out[storage] = (rho, u)
-    (r64, u64), (r, u) = out["f64"], out[args.storage]
-    return {"vs": "library FP64 path", "size": "x".join(map(str, dims)), "steps": steps,
-            "rho_rel_l2": float(torch.linalg.norm(r - r64) / torch.linalg.norm(r64)),
-            "u_rel_l2": float(torch.linalg.norm(u - u64) / torch.linalg.norm(u64))}
+    lattice = w["lattice"]
+    if lattice == "D2Q9":
+        faces = faces[:4] + [0, 0]
+    rdims = (1, dims[1], 1) if w["flow"] == "channel" else dims
+    rcfg = oracle.make_cfg(lattice, rdims, w["tau"], force=force_of(ws), faces=faces, wall_u=wall_u)
+    rho, u, pineq = parity_fields(ws, rdims)
+    f = oracle.init(rcfg, rho, u, pineq)
+    t0 = time.perf_counter()
+    f = oracle.run(rcfg, f, steps, threads)
+    dt_ref = time.perf_counter() - t0
+    ref = oracle.moments(rcfg, f)
+    # timing sample: the parity run itself, extended on the full parity box
+    if w["flow"] == "channel":
+        tcfg = oracle.make_cfg(lattice, dims, w["tau"], force=force_of(ws), faces=faces, wall_u=wall_u)
+        rho, u, pineq = parity_fields(ws, dims)
+        ft = oracle.init(tcfg, rho, u, pineq)
+        timed_updates, dt = 0, 0.0
+    else:
+        tcfg, ft = rcfg, f
+        timed_updates, dt = dims[0] * dims[1] * dims[2] * steps, dt_ref
+    N = dims[0] * dims[1] * dims[2]
+    extra = 0
+    while dt < budget_s:
+        t0 = time.perf_counter()
+        ft = oracle.run(tcfg, ft, 10, threads)
+        dt += time.perf_counter() - t0
+        timed_updates += N * 10
+        extra += 10
+    used = threads if threads > 0 else oracle.max_threads()
+    sample = "%s %s %s, %d timed steps (FP64 oracle, two arrays, OpenMP); its %d-step state is the accuracy " \
+             "reference" % (lattice, w["flow"], "x".join(map(str, dims)), timed_updates // N, steps)
+    cpu = {"value": timed_updates / dt / 1e6, "unit": "MLUPS", "cores": used, "kind": "oracle", "sample": sample}
+    return cpu, ref
+
+
+def side_accuracy(w, args, torch, ref):
+    """The benchmark's storage and scheme at the parity size of its flow, from
+    the same initial fields as the oracle run of the CPU-baseline leg, against
+    that FP64 oracle result: relative L2 of rho, rho - rho0 and u."""
+    from paper_2304_06437_gb300 import Solver
+    dims, steps = PARITY_SIZE[w["flow"]]
+    ws = dict(w)
+    ws["dims"] = dims
+    if w["flow"] == "channel":
+        ws["force"] = 1e-6
+    faces, wall_u = boundary(ws)
+    s = Solver(w["lattice"], dims, w["tau"], faces=faces, wall_u=wall_u, storage=args.storage,
+               scheme=args.scheme, force=force_of(ws))
+    rho0, u0, pi0 = parity_fields(ws, dims)
+    s.init_moments(rho0, np.ascontiguousarray(u0), None if pi0 is None else np.ascontiguousarray(pi0))
+    s.step(steps)
+    rho, u = s.moments()
+    s.close()
+    r_ref, u_ref = ref
+    if w["flow"] == "channel":  # the column's fields, repeated over x and z
+        nx, ny, nz = dims
+        r_ref = np.broadcast_to(r_ref.reshape(1, ny, 1), (nz, ny, nx)).reshape(-1)
+        u_ref = np.broadcast_to(u_ref.reshape(-1, 1, ny, 1), (u_ref.shape[0], nz, ny, nx)).reshape(u_ref.shape[0], -1)
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    return {"vs": "FP64 CPU oracle", "size": "x".join(map(str, dims)), "steps": steps,
+            "rho_rel_l2": rel(rho, r_ref), "drho_rel_l2": rel(rho - 1.0, r_ref - 1.0) if np.any(r_ref != 1.0)
+            else None, "u_rel_l2": rel(u, u_ref)}
 
 
 def measure_e2e(s, w, args, torch, stream):

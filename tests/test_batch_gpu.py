@@ -5,14 +5,18 @@ static work list of all domains' bricks, replayed from a CUDA graph two steps
 at a time.  Every domain must come out bit for bit equal to stepping it alone
 (same per-node arithmetic, bricks and shells), for odd and even step counts,
 with members that were also stepped alone in between, and with several
-classes (lattices, storages, forcing) in one batch.  The solo path itself is
-held to the CPU oracle by the parity tests.
+classes (lattices, storages, forcing) in one batch.  Every member is also
+held directly to the CPU oracle: FP64 and FP32 members by the relative L2
+error of rho and u (1e-12 / 1e-5), FP16 / BF16 members step by step within
+one unit of the storage format of the rounded oracle step.
 """
 import numpy as np
 import pytest
 
+import oracle
 import synth
-from lbcase import faces_for, random_state
+from lbcase import faces_for, oracle_cfg, random_state, rel_l2
+from oracle.storage import quantum, round_populations
 
 pytestmark = pytest.mark.gpu
 
@@ -109,4 +113,45 @@ def test_batch_rejects_unsupported(lb):
         with pytest.raises(lb.LBError):
             lb.Batch(bad)
     for s in (s2p, s32):
+        s.close()
+
+
+def test_batch_members_match_oracle(lb):
+    """The batched kernel has its own argument table, work list and per-domain
+    parity: each member is compared with the oracle run of its own input."""
+    specs = _specs(99)
+    f0s, cfgs, members = [], [], []
+    for i, sp in enumerate(specs):
+        faces, wall_u = faces_for(sp["lat"], sp["fname"])
+        force = (2e-5, 1e-5, 0.0) if sp["fname"] == "duct" else (0, 0, 0)
+        w = oracle.lattice_tables(sp["lat"])[1]
+        # the stored initial state (set_populations rounds to the storage)
+        f0s.append(round_populations(random_state(sp["lat"], sp["dims"], 500 + i), w, sp["storage"]))
+        cfgs.append(oracle_cfg(sp["lat"], sp["dims"], sp["tau"], faces, wall_u, force=force))
+        members.append(_make(lb, sp, 500 + i))
+    prev = [f.copy() for f in f0s]
+    with lb.Batch(members) as b:
+        for step in range(3):
+            b.step(1)
+            b.sync()
+            for sp, s, cfg, i in zip(specs, members, cfgs, range(len(specs))):
+                if sp["storage"] not in ("f16s", "bf16s"):
+                    continue
+                w = oracle.lattice_tables(sp["lat"])[1]
+                got = s.get_populations()
+                ref = oracle.run_stored(cfg, prev[i], 1, sp["storage"])
+                dg, dr = got - w[:, None], ref - w[:, None]
+                ulp = np.maximum(quantum(dg, sp["storage"]), quantum(dr, sp["storage"]))
+                assert (np.abs(dg - dr) <= ulp * (1 + 1e-12) + 1e-7).all(), (i, step)
+                prev[i] = got
+        b.step(4)
+        b.sync()
+        for sp, s, cfg, f0 in zip(specs, members, cfgs, f0s):
+            if sp["storage"] not in ("f64", "f32"):
+                continue
+            r_ref, u_ref = oracle.moments(cfg, oracle.run(cfg, f0, 7))
+            r, u = s.moments()
+            tol = 1e-12 if sp["storage"] == "f64" else 1e-5
+            assert rel_l2(r, r_ref) < tol and rel_l2(u, u_ref) < tol, (sp, rel_l2(r, r_ref), rel_l2(u, u_ref))
+    for s in members:
         s.close()

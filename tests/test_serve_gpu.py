@@ -5,10 +5,18 @@ admitted between rounds as memory allows and stepped together in one batch.
 Each request's result must equal solving it alone with the same round length
 and convergence rule (bit for bit: the batch is bitwise equal to solo
 stepping and the convergence decision depends on the request's own state).
-Admission under a memory limit must delay, not drop, requests.
+Admission under a memory limit must delay, not drop, requests.  Each served
+result is also compared with the FP64 CPU oracle run from the same rest state
+for the same number of steps: relative L2 of rho and u within 1e-5 for FP32
+storage; FP16 storage is held to 1e-2 on u (its stated error, a few 1e-4 on
+the channel study, grows with the lid speed and the run length; the gate only
+catches a wrong result, not a rounding difference).
 """
 import numpy as np
 import pytest
+
+import oracle
+from lbcase import rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -60,6 +68,16 @@ def test_served_results_equal_solo(lb):
         assert r.steps == steps
         assert r.residual == res
         assert np.array_equal(r.rho, rho) and np.array_equal(r.u, u)
+    # the served results against the oracle (rest start, same step count)
+    for r in done:
+        cfg = oracle.make_cfg(r.lattice, r.dims, r.tau, force=r.force, faces=r.faces, wall_u=r.wall_u)
+        n = int(np.prod(r.dims))
+        # lb_create's state: every population at its rest value t_a rho0
+        f0 = np.repeat(oracle.lattice_tables(r.lattice)[1][:, None], n, axis=1)
+        r_ref, u_ref = oracle.moments(cfg, oracle.run(cfg, f0, r.steps))
+        tol_u = 1e-5 if r.storage == "f32" else 1e-2
+        assert rel_l2(r.rho, r_ref) < (1e-5 if r.storage == "f32" else 1e-3)
+        assert rel_l2(r.u, u_ref) < tol_u, (r.rid, r.storage, rel_l2(r.u, u_ref))
 
 
 def test_admission_waits_for_memory(lb):
