@@ -66,7 +66,10 @@ extern "C" {
 #define LB_E_TOO_LARGE (-7)   /* grid exceeds the fixed scratch of lb_step_noalloc */
 
 typedef enum { LB_D2Q9 = 0, LB_D3Q19 = 1, LB_D3Q27 = 2 } lb_lattice;
-typedef enum { LB_PERIODIC = 0, LB_WALL = 1, LB_MOVING_WALL = 2 } lb_face_kind;
+/* LB_LINK: the face borders the slab of another context (a rank boundary of
+ * the slab decomposition below); only the two faces of the slowest axis (z in
+ * 3D, y in 2D) and only with the fused scheme. */
+typedef enum { LB_PERIODIC = 0, LB_WALL = 1, LB_MOVING_WALL = 2, LB_LINK = 3 } lb_face_kind;
 
 /* Storage precision of the population array.  Every mode stores the shifted
  * population f_a - t_a rho0 (exact in FP64; the accurate representation in the
@@ -158,8 +161,12 @@ LB_API int lb_moments(lb_ctx* ctx, double* rho, double* u, int32_t on_device);
 /* FP64 on-device reductions over all nodes: total mass sum rho, total momentum
  * sum_a f_a c_a (without the F/2 shift), and -- if residual is not NULL -- the
  * relative velocity change ||u - u_prev||_2 / ||u||_2 since the previous call
- * that asked for it (1.0 on the first such call).  Deterministic (fixed
- * reduction order).  Returns LB_E_DIVERGED if a value is not finite. */
+ * that asked for it (1.0 on the first such call, and on the first after the
+ * state was set by lb_init_moments / lb_init_uniform / lb_set_populations).
+ * u_prev is kept as an FP32 snapshot (12 bytes per node, allocated on the
+ * first such call), so the residual is that of the exact u_prev within
+ * 2^-24 ||u_prev|| / ||u||.  Deterministic (fixed reduction order).  Returns
+ * LB_E_DIVERGED if a value is not finite. */
 LB_API int lb_reduce(lb_ctx* ctx, double* mass, double mom[3], double* residual);
 
 /* Waits for the context stream; reports a sticky kernel status (LB_E_TIMEOUT). */
@@ -373,6 +380,69 @@ LB_API int lb_cg_set_nci(lb_cg* c, double amplitude, double eps, int32_t h);
  * default stream; synchronises the device.  Errors: LB_E_INVAL, LB_E_NOMEM,
  * LB_E_CUDA. */
 LB_API int lb_selftest_timeout(int64_t limit_ns, int64_t* waited_ns);
+
+/* ------------------------------------------------------------------ slabs
+ * Domain decomposition along the slowest axis (z in 3D, y in 2D), the
+ * multi-GPU form of the method (the paper names multi-GPU scaling as its
+ * future work, section 7).  Each rank owns a slab -- a context whose faces on
+ * that axis are LB_LINK where it borders another slab -- and a rank boundary
+ * is just another brick face of the fused scheme: the post-collision
+ * populations that leave a slab through it are the shell records the
+ * neighbouring slab's boundary bricks read in the next launch.  They travel
+ * as one message per link face and step:
+ *   sender:   lb_halo_pack(ctx, side, buf)      side 0 = low face, 1 = high face
+ *   transport (a device copy on one GPU, NCCL send/recv between GPUs)
+ *   receiver: lb_halo_unpack(ctx, 1 - side, buf)
+ * after which the receiver takes one step, lb_step(ctx, 1) (a linked context
+ * rejects n > 1: its halo is stale after one launch).  The message holds, for
+ * the sender's outermost plane, its x- and y-face shell records (the lateral
+ * populations of the neighbouring bricks, which the receiver needs for its
+ * diagonal links) and the z-face records of its outermost brick row; the
+ * receiver stores them in ghost slots of its shell, so no slab ever writes
+ * another's memory.  Every slab computes the same bits as the single domain
+ * (the shell records are the neighbour's rounded state collided once more).
+ *
+ * lb_halo_bytes: size of one message of ctx (equal on both sides of a
+ *   boundary when the slabs share lattice, storage, the extents of the two
+ *   other axes and the brick cross-section).
+ * lb_halo_pack: enqueues on the context stream the copy of the records that
+ *   leave through face `side` of the current state into buf (device memory
+ *   of the context's device, lb_halo_bytes, 16-byte aligned), preceded by a
+ *   64-byte header naming the layout.
+ * lb_halo_unpack: enqueues the copy of a neighbour's message into the ghost
+ *   slots of face `side`.  If the header does not match this context (other
+ *   lattice, precision, extents, brick cross-section, or a message packed for
+ *   the same side), nothing is copied and the kernel records LB_E_INVAL,
+ *   which the next lb_sync() returns.
+ * Errors: LB_E_INVAL (NULL, side not 0/1, face `side` not LB_LINK), LB_E_CUDA. */
+LB_API int lb_halo_bytes(const lb_ctx* ctx, int64_t* bytes);
+LB_API int lb_halo_pack(lb_ctx* ctx, int32_t side, void* buf);
+LB_API int lb_halo_unpack(lb_ctx* ctx, int32_t side, const void* buf);
+
+/* A slab group: the decomposition run in one process on one device, one
+ * context and one stream per rank -- the stand-in for one rank per GPU, with
+ * the message copies on the device in place of NCCL.  lb_group_create cuts
+ * the domain (arguments as for lb_create) into nranks slabs along the slowest
+ * axis, counts[r] planes each (NULL: as even as possible; every count >= 1,
+ * summing to the extent); faces between slabs become LB_LINK, and a periodic
+ * slowest axis links the last slab to the first (a single rank then links to
+ * itself).  Every rank uses the brick cross-section of rank 0; opt->stream is
+ * ignored (each rank gets a library-owned stream).  Errors as for lb_create,
+ * plus LB_E_INVAL for bad counts.
+ * lb_group_rank: rank r's context (owned by the group: initialise and read it
+ *   with the calls above; its node range is the global one from *offset
+ *   planes on, in the canonical layout a contiguous range of nodes).
+ * lb_group_step: n steps; per step every rank packs its link faces, waits
+ *   (by events) for its neighbours' messages, unpacks them and launches its
+ *   step, and a rank packs again only after its neighbours unpacked.
+ * lb_group_sync: waits for every rank; returns the first non-OK status. */
+typedef struct lb_group lb_group;
+LB_API int lb_group_create(int32_t lattice, const int64_t dims[3], double tau, const lb_boundary* bnd,
+                           const lb_options* opt, int32_t nranks, const int64_t* counts, lb_group** out);
+LB_API int lb_group_rank(lb_group* grp, int32_t rank, lb_ctx** ctx, int64_t* offset);
+LB_API int lb_group_step(lb_group* grp, int64_t n);
+LB_API int lb_group_sync(lb_group* grp);
+LB_API void lb_group_destroy(lb_group* grp);
 
 /* Human-readable name of a status code. */
 LB_API const char* lb_status_string(int code);

@@ -5,6 +5,7 @@ built for sm_103a by :mod:`paper_2304_06437_gb300.build`.  This package only
 binds it; there is no CPU fallback.
 """
 from ._binding import LBError, load  # noqa: F401
-from .solver import Batch, CGSolver, Solver, fused_plan, lattice_table, memory_plan  # noqa: F401
+from .solver import Batch, CGSolver, SlabGroup, Solver, fused_plan, lattice_table, memory_plan  # noqa: F401
 
-__all__ = ["Solver", "Batch", "CGSolver", "LBError", "fused_plan", "lattice_table", "memory_plan", "load"]
+__all__ = ["Solver", "Batch", "CGSolver", "SlabGroup", "LBError", "fused_plan", "lattice_table", "memory_plan",
+           "load"]

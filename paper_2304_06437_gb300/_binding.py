@@ -23,7 +23,7 @@ LB_E_TOO_LARGE = -7
 LB_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 LB_D2Q9, LB_D3Q19, LB_D3Q27 = 0, 1, 2
-LB_PERIODIC, LB_WALL, LB_MOVING_WALL = 0, 1, 2
+LB_PERIODIC, LB_WALL, LB_MOVING_WALL, LB_LINK = 0, 1, 2, 3
 LB_F64, LB_F32, LB_F16S, LB_BF16S = 0, 1, 2, 3
 LB_SCHEME_FUSED, LB_SCHEME_TWO_PASS = 0, 1
 
@@ -160,6 +160,15 @@ SIGNATURES = {
     "lb_cg_set_nci": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int32]),
     "lb_plan_fused": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _i64p, _P(ctypes.c_int32), ctypes.c_int32,
                                      _P(lb_plan_t)]),
+    "lb_halo_bytes": (ctypes.c_int, [_vp, _i64p]),
+    "lb_halo_pack": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
+    "lb_halo_unpack": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
+    "lb_group_create": (ctypes.c_int, [ctypes.c_int32, _i64p, ctypes.c_double, _P(lb_boundary), _P(lb_options),
+                                       ctypes.c_int32, _i64p, _P(_vp)]),
+    "lb_group_rank": (ctypes.c_int, [_vp, ctypes.c_int32, _P(_vp), _i64p]),
+    "lb_group_step": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "lb_group_sync": (ctypes.c_int, [_vp]),
+    "lb_group_destroy": (None, [_vp]),
     "lb_selftest_timeout": (ctypes.c_int, [ctypes.c_int64, _i64p]),
     "lb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lb_abi_version": (ctypes.c_int, []),

@@ -268,6 +268,8 @@ int lb_batch_create(lb_ctx* const* ctxs, int32_t n, void* stream, lb_batch** out
     lb_ctx* x = ctxs[i];
     if (!x || x->device != dev) return LB_E_INVAL;
     if (x->scheme != LB_SCHEME_FUSED) return LB_E_UNSUPPORTED;
+    // a slab bordering others steps between halo exchanges, not in a batch
+    if (x->g.zlink[0] || x->g.zlink[1]) return LB_E_UNSUPPORTED;
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == x) return LB_E_INVAL;
     const K1Variant* v = k1_ctx_variant(x);

@@ -324,13 +324,22 @@ int lb_create(int32_t lattice, const int64_t dims[3], double tau, const lb_bound
   else std::memset(&b, 0, sizeof(b));
   for (int ax = 0; ax < 3; ++ax) {
     const int lo = b.kind[2 * ax], hi = b.kind[2 * ax + 1];
-    if (lo < 0 || lo > 2 || hi < 0 || hi > 2) return LB_E_INVAL;
+    if (lo < 0 || lo > LB_LINK || hi < 0 || hi > LB_LINK) return LB_E_INVAL;
     if ((lo == LB_PERIODIC) != (hi == LB_PERIODIC)) return LB_E_INVAL;
   }
   if (d == 2 && (b.kind[4] != LB_PERIODIC || b.kind[5] != LB_PERIODIC)) {
     // the z faces of a 2D grid carry no velocities; accept any kind but ignore it
     b.kind[4] = b.kind[5] = LB_PERIODIC;
   }
+  // link faces: only the two faces of the slowest axis (z in 3D, y in 2D),
+  // and only with the fused scheme
+  bool any_link = false;
+  for (int f = 0; f < 6; ++f) {
+    if (b.kind[f] != LB_LINK) continue;
+    if (f / 2 != d - 1) return LB_E_INVAL;
+    any_link = true;
+  }
+  if (any_link && opt.scheme != LB_SCHEME_FUSED) return LB_E_UNSUPPORTED;
 
   lb_ctx* ctx = new (std::nothrow) lb_ctx();
   if (!ctx) return LB_E_NOMEM;
@@ -377,6 +386,7 @@ int lb_create(int32_t lattice, const int64_t dims[3], double tau, const lb_bound
   }
   g.has_force = g.force[0] != 0.0 || g.force[1] != 0.0 || g.force[2] != 0.0;
   for (int ax = 0; ax < 3; ++ax) g.per[ax] = g.face_kind[2 * ax] == LB_PERIODIC ? 1 : 0;
+  for (int k = 0; k < 2; ++k) g.zlink[k] = g.face_kind[4 + k] == LB_LINK ? 1 : 0;
   g.pitch = (int64_t(g.nx) + 31) / 32 * 32;
   g.vol = g.pitch * g.ny * g.nz;
 
@@ -589,6 +599,8 @@ int lb_get_region(lb_ctx* ctx, const int64_t lo[3], const int64_t size[3], doubl
 
 int lb_step(lb_ctx* ctx, int64_t n) {
   if (!ctx || n < 0) return LB_E_INVAL;
+  // a slab bordering others takes one step between two halo exchanges
+  if (n > 1 && (ctx->g.zlink[0] || ctx->g.zlink[1])) return LB_E_INVAL;
   DeviceGuard guard(ctx->device);
   for (int64_t i = 0; i < n; ++i) {
     cudaError_t e = ctx->scheme == LB_SCHEME_FUSED ? k1_step(ctx) : k0_step(ctx);

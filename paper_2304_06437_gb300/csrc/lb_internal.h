@@ -19,6 +19,7 @@ struct Geometry {
   int64_t pitch;           // elements per stored row (>= nx, multiple of 32)
   int64_t vol;             // elements per population: pitch * ny * nz
   int per[3];              // periodic flag per internal axis
+  int zlink[2];            // internal -z / +z face borders another slab (LB_LINK)
   int face_kind[6];        // internal faces -x,+x,-y,+y,-z,+z
   double wall_u[6][3];     // internal components
   double tau, rho0;
@@ -31,6 +32,7 @@ struct FusedPlan {
   int bx, by, bz;          // brick cross-section and sweep length
   int nbx, nby, nbz;
   int nxf, nyf, nzf;       // directions crossing an x / y / z face (per side)
+  int zg;                  // 1: ghost planes / brick rows for link faces (see K1Args)
   int64_t sx_elems, sy_elems, sz_elems;  // per parity
   int64_t parity_elems;
   int slots;               // TMA pipeline depth

@@ -51,6 +51,14 @@ struct K1Args {
   int nx, ny, nz;
   int64_t pitch, vol;
   int per[3];
+  // z faces that border another context's slab (a rank boundary): their
+  // incoming shell records sit in ghost slots -- plane -1 / nz of the x and
+  // y records, brick row -1 / nbz of the z records -- filled between
+  // launches by lb_halo_unpack.  zg = 1 when a context has ghost slots (the
+  // shell's planes and brick rows are then shifted by one), nzs = nz + 2 zg
+  // planes per x / y record, nbzs = nbz + 2 zg brick rows per z-record side.
+  int zlink[2];
+  int zg, nzs, nbzs;
   int bz, nbx, nby, nbz;
   void* f;
   const R* sh_cur;
@@ -239,11 +247,11 @@ __device__ __forceinline__ void export_node(const K1Args<R>& args, const R (&fin
   Coef<R> kc;
   coeffs<L, R, FORCE>(m, args.ph, kc);
   R* shn = args.sh_next;
-  const int64_t nzy = int64_t(args.nz) * args.ny, nzx = int64_t(args.nz) * args.nx;
+  const int64_t nzy = int64_t(args.nzs) * args.ny, nzx = int64_t(args.nzs) * args.nx;
   const int64_t nyx = int64_t(args.ny) * args.nx;
   if (faces & (kFaceW | kFaceE)) {
-    // SX[side][I][ia][z][y]
-    const int64_t row = int64_t(zd) * args.ny + y;
+    // SX[side][I][ia][z + zg][y]
+    const int64_t row = int64_t(zd + args.zg) * args.ny + y;
     if (faces & kFaceW)
       export_face<L, R, 0, -1>(kc, {shn + args.sx_off + (int64_t(bI) * NXF) * nzy + row, nzy});
     if (faces & kFaceE)
@@ -251,8 +259,8 @@ __device__ __forceinline__ void export_node(const K1Args<R>& args, const R (&fin
   }
   if constexpr (NYF > 0) {
     if (faces & (kFaceS | kFaceN)) {
-      // SY[side][J][ia][z][x]
-      const int64_t row = int64_t(zd) * args.nx + x;
+      // SY[side][J][ia][z + zg][x]
+      const int64_t row = int64_t(zd + args.zg) * args.nx + x;
       if (faces & kFaceS)
         export_face<L, R, 1, -1>(kc, {shn + args.sy_off + (int64_t(bJ) * NYF) * nzx + row, nzx});
       if (faces & kFaceN)
@@ -260,12 +268,12 @@ __device__ __forceinline__ void export_node(const K1Args<R>& args, const R (&fin
     }
   }
   if (faces & (kFaceD | kFaceU)) {
-    // SZ[side][K][ia][y][x]
+    // SZ[side][K + zg][ia][y][x]
     const int64_t row = int64_t(y) * args.nx + x;
     if (faces & kFaceD)
-      export_face<L, R, 2, -1>(kc, {shn + args.sz_off + (int64_t(bK) * NZF) * nyx + row, nyx});
+      export_face<L, R, 2, -1>(kc, {shn + args.sz_off + (int64_t(bK + args.zg) * NZF) * nyx + row, nyx});
     if (faces & kFaceU)
-      export_face<L, R, 2, 1>(kc, {shn + args.sz_off + ((int64_t(args.nbz) + bK) * NZF) * nyx + row, nyx});
+      export_face<L, R, 2, 1>(kc, {shn + args.sz_off + ((int64_t(args.nbzs) + bK + args.zg) * NZF) * nyx + row, nyx});
   }
 }
 
@@ -355,11 +363,13 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   const bool nbE = x0 + bxa < nx || args.per[0];
   const bool nbS = y0 > 0 || args.per[1];
   const bool nbN = y0 + bya < ny || args.per[1];
-  const bool nbD = z0 > 0 || args.per[2];
-  const bool nbU = z1 < nz || args.per[2];
+  const bool nbD = z0 > 0 || args.per[2] || args.zlink[0];
+  const bool nbU = z1 < nz || args.per[2] || args.zlink[1];
   const int bIw = (bI + nbx - 1) % nbx, bIe = (bI + 1) % nbx;
   const int bJs = (bJ + nby - 1) % nby, bJn = (bJ + 1) % nby;
-  const int bKd = (bK + nbz - 1) % nbz, bKu = (bK + 1) % nbz;
+  // the brick rows below / above (a link face's ghost row is -1 / nbz)
+  const int bKd = args.per[2] ? (bK + nbz - 1) % nbz : bK - 1;
+  const int bKu = args.per[2] ? (bK + 1) % nbz : bK + 1;
 
   // bounce-back predicates of this node along x and y: the upstream point of
   // a direction with c = +1 is x - 1, which leaves a non-periodic low face at x = 0
@@ -368,7 +378,9 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   const bool bylo = active && (y == 0) && !args.per[1];
   const bool byhi = active && (y == ny - 1) && !args.per[1];
   const bool xy_wall = bxlo || bxhi || bylo || byhi;
-  const bool z_walls = !args.per[2];
+  // walls at the z faces (neither periodic nor a link to another slab)
+  const bool zwall_lo = !args.per[2] && !args.zlink[0];
+  const bool zwall_hi = !args.per[2] && !args.zlink[1];
 
   S* __restrict__ fglob = static_cast<S*>(args.f);
   const R* __restrict__ shc = args.sh_cur;
@@ -447,7 +459,8 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
         const int side = west ? 1 : 0;
         const int bb = west ? bIw : bIe;
         hval[e] = ok;
-        hbase[e] = args.sx_off + ((int64_t(side) * nbx + bb) * NXF + ia) * int64_t(nz) * ny + sy;
+        hbase[e] = args.sx_off + ((int64_t(side) * nbx + bb) * NXF + ia) * int64_t(args.nzs) * ny +
+                   int64_t(args.zg) * ny + sy;
         hzs[e] = ny;
         hsm[e] = (west ? lat_slot_of_sub<L, 0, 1>(ia) : lat_slot_of_sub<L, 0, -1>(ia)) * WPLANE + r * WX + col;
       } else {
@@ -461,7 +474,8 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
         const int side = south ? 1 : 0;
         const int bb = south ? bJs : bJn;
         hval[e] = ok;
-        hbase[e] = args.sy_off + ((int64_t(side) * nby + bb) * NYF + ia) * int64_t(nz) * nx + x0 + i;
+        hbase[e] = args.sy_off + ((int64_t(side) * nby + bb) * NYF + ia) * int64_t(args.nzs) * nx +
+                   int64_t(args.zg) * nx + x0 + i;
         hzs[e] = nx;
         hsm[e] = (south ? lat_slot_of_sub<L, 1, 1>(ia) : lat_slot_of_sub<L, 1, -1>(ia)) * WPLANE + row * WX + 1 + i;
       }
@@ -478,7 +492,8 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   // ring values of two planes ahead in registers: ha = plane being produced,
   // hb = the next one (loads in flight for about two planes).  The entry
   // pointers walk up one plane per call; planes below 0 or above nz - 1 only
-  // occur for periodic z and wrap.
+  // occur for periodic z, and wrap, or at a link face, where they are the
+  // ghost planes -1 / nz.
   R ha[HPT], hb[HPT];
   const R* hptr[HPT];
 #pragma unroll
@@ -489,9 +504,10 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
       if (!hval[e]) hsm[e] = -1;
     }
   }
+  const bool zwrap = args.per[2] != 0;
   auto halo_fetch = [&](R(&dst)[HPT], int z) {
     const bool ok = z <= z1 && plane_needed(z);
-    const int zw = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+    const int zw = !zwrap ? z : (z < 0 ? z + nz : (z >= nz ? z - nz : z));
 #pragma unroll
     for (int e = 0; e < HPT; ++e) {
       if constexpr (Sh::HSMEM) {
@@ -519,7 +535,7 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
 
   // export of the staged lateral perimeter of plane zx (whole warps)
   // resolve each perimeter node's shell records once per brick
-  const int64_t nzy = int64_t(nz) * ny, nzx = int64_t(nz) * nx;
+  const int64_t nzy = int64_t(args.nzs) * ny, nzx = int64_t(args.nzs) * nx;
   if (exp_warp) {
 #pragma unroll 1
     for (int e = exp_lane; e < PE; e += 32 * Sh::NEXW) {
@@ -532,8 +548,10 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
       const bool ok = nb && (xface ? pty < bya : ptx < bxa) && k < (xface ? Sh::SEGY : Sh::SEGX);
       // SX[side][I][ia][z][y], SY[side][J][ia][z][x]; the high face (E, N)
       // is the side-1 record, a brick-uniform distance further
-      desc_off[e] = xface ? args.sx_off + ((int64_t(face == 1 ? nbx : 0) + bI) * NXF) * nzy + (y0 + pty)
-                          : args.sy_off + ((int64_t(face == 3 ? nby : 0) + bJ) * NYF) * nzx + (x0 + ptx);
+      desc_off[e] = xface ? args.sx_off + ((int64_t(face == 1 ? nbx : 0) + bI) * NXF) * nzy +
+                                int64_t(args.zg) * ny + (y0 + pty)
+                          : args.sy_off + ((int64_t(face == 3 ? nby : 0) + bJ) * NYF) * nzx +
+                                int64_t(args.zg) * nx + (x0 + ptx);
       desc_p[e] = ok ? perimeter_index<NYF>(ptx, pty, bxa, bya) : -1;
     }
   }
@@ -591,7 +609,8 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
       const bool low = (c == z0 - 1);
       const int side = low ? 1 : 0;
       const int bb = low ? bKd : bKu;
-      const int64_t base = args.sz_off + (int64_t(side) * nbz + bb) * NZF * int64_t(ny) * nx + int64_t(y) * nx + x;
+      const int64_t base =
+          args.sz_off + (int64_t(side) * args.nbzs + bb + args.zg) * NZF * int64_t(ny) * nx + int64_t(y) * nx + x;
       onl[0] = onl[1] = onl[2] = R(0);
       static_for<0, Q>([&](auto A_) {
         constexpr int a = decltype(A_)::value;
@@ -727,8 +746,8 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
         bdn_mask = 0;
       }
       // halfway bounce-back for destination plane g (threads next to a wall)
-      if (real_g && active && (xy_wall || (z_walls && (g == 0 || g == nz - 1)))) {
-        const bool bzlo = z_walls && g == 0, bzhi = z_walls && g == nz - 1;
+      if (real_g && active && (xy_wall || (zwall_lo && g == 0) || (zwall_hi && g == nz - 1))) {
+        const bool bzlo = zwall_lo && g == 0, bzhi = zwall_hi && g == nz - 1;
         static_for<0, Q>([&](auto A_) {
           constexpr int a = decltype(A_)::value;
           constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
@@ -915,8 +934,8 @@ __global__ void __launch_bounds__(256) k1_bootstrap(const __grid_constant__ K1Ar
     const bool eE = x == x0 + bxa - 1 && (x0 + bxa < args.nx || args.per[0]);
     const bool eS = y == y0 && (y0 > 0 || args.per[1]);
     const bool eN = y == y0 + bya - 1 && (y0 + bya < args.ny || args.per[1]);
-    const bool eD = z == z0 && (z0 > 0 || args.per[2]);
-    const bool eU = z == z1 - 1 && (z1 < args.nz || args.per[2]);
+    const bool eD = z == z0 && (z0 > 0 || args.per[2] || args.zlink[0]);
+    const bool eU = z == z1 - 1 && (z1 < args.nz || args.per[2] || args.zlink[1]);
     if (!(eW || eE || eS || eN || eD || eU)) continue;
     const int64_t o = x + args.pitch * (y + int64_t(args.ny) * z);
     const S* fg = static_cast<const S*>(args.f);

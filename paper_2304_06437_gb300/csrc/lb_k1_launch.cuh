@@ -51,6 +51,11 @@ K1Args<R> k1_make_args(lb_ctx* ctx, int cur_parity, int next_parity) {
   a.pitch = g.pitch;
   a.vol = g.vol;
   for (int k = 0; k < 3; ++k) a.per[k] = g.per[k];
+  a.zlink[0] = g.zlink[0];
+  a.zlink[1] = g.zlink[1];
+  a.zg = p.zg;
+  a.nzs = g.nz + 2 * p.zg;
+  a.nbzs = p.nbz + 2 * p.zg;
   a.bz = p.bz;
   a.nbx = p.nbx;
   a.nby = p.nby;

@@ -135,9 +135,12 @@ static void fill_plan(const Geometry& g, const K1Variant* v, int req_bz, FusedPl
   p.nxf = nxf;
   p.nyf = nyf;
   p.nzf = nzf;
-  p.sx_elems = 2LL * p.nbx * nxf * int64_t(g.nz) * g.ny;
-  p.sy_elems = 2LL * p.nby * nyf * int64_t(g.nz) * g.nx;
-  p.sz_elems = 2LL * p.nbz * nzf * int64_t(g.ny) * g.nx;
+  // a link face's incoming records sit in one ghost plane (x / y records)
+  // and one ghost brick row (z records) on each side of the shell
+  p.zg = (g.zlink[0] || g.zlink[1]) ? 1 : 0;
+  p.sx_elems = 2LL * p.nbx * nxf * int64_t(g.nz + 2 * p.zg) * g.ny;
+  p.sy_elems = 2LL * p.nby * nyf * int64_t(g.nz + 2 * p.zg) * g.nx;
+  p.sz_elems = 2LL * (p.nbz + 2 * p.zg) * nzf * int64_t(g.ny) * g.nx;
   p.parity_elems = ((p.sx_elems + p.sy_elems + p.sz_elems) + 31) / 32 * 32;
   *plan = p;
 }

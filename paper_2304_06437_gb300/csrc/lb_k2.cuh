@@ -169,11 +169,13 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
   const bool nbE = x0 + bxa < nx || args.per[0];
   const bool nbS = y0 > 0 || args.per[1];
   const bool nbN = y0 + bya < ny || args.per[1];
-  const bool nbD = z0 > 0 || args.per[2];
-  const bool nbU = z1 < nz || args.per[2];
+  const bool nbD = z0 > 0 || args.per[2] || args.zlink[0];
+  const bool nbU = z1 < nz || args.per[2] || args.zlink[1];
   const int bIw = (bI + nbx - 1) % nbx, bIe = (bI + 1) % nbx;
   const int bJs = (bJ + nby - 1) % nby, bJn = (bJ + 1) % nby;
-  const int bKd = (bK + nbz - 1) % nbz, bKu = (bK + 1) % nbz;
+  // the brick rows below / above (a link face's ghost row is -1 / nbz)
+  const int bKd = args.per[2] ? (bK + nbz - 1) % nbz : bK - 1;
+  const int bKu = args.per[2] ? (bK + 1) % nbz : bK + 1;
 
   // bounce-back predicates per lane (x is even, so only lane .x can sit on x = 0)
   const bool bxlo0 = act0 && (x == 0) && !args.per[0];
@@ -182,7 +184,9 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
   const bool bylo = act0 && (y == 0) && !args.per[1];
   const bool byhi = act0 && (y == ny - 1) && !args.per[1];
   const bool xy_wall = bxlo0 || bxhi0 || bxhi1 || bylo || byhi;
-  const bool z_walls = !args.per[2];
+  // walls at the z faces (neither periodic nor a link to another slab)
+  const bool zwall_lo = !args.per[2] && !args.zlink[0];
+  const bool zwall_hi = !args.per[2] && !args.zlink[1];
 
   S* __restrict__ fglob = static_cast<S*>(args.f);
   const R* __restrict__ shc = args.sh_cur;
@@ -234,7 +238,8 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
         const int side = west ? 1 : 0;
         const int bb = west ? bIw : bIe;
         hval[e] = ok;
-        hbase[e] = args.sx_off + ((int64_t(side) * nbx + bb) * NXF + ia) * int64_t(nz) * ny + sy;
+        hbase[e] = args.sx_off + ((int64_t(side) * nbx + bb) * NXF + ia) * int64_t(args.nzs) * ny +
+                   int64_t(args.zg) * ny + sy;
         hzs[e] = ny;
         hsm[e] = (west ? lat_slot_of_sub<L, 0, 1>(ia) : lat_slot_of_sub<L, 0, -1>(ia)) * WPLANE + r * WX + col;
       } else {
@@ -248,7 +253,8 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
         const int side = south ? 1 : 0;
         const int bb = south ? bJs : bJn;
         hval[e] = ok;
-        hbase[e] = args.sy_off + ((int64_t(side) * nby + bb) * NYF + ia) * int64_t(nz) * nx + x0 + i;
+        hbase[e] = args.sy_off + ((int64_t(side) * nby + bb) * NYF + ia) * int64_t(args.nzs) * nx +
+                   int64_t(args.zg) * nx + x0 + i;
         hzs[e] = nx;
         hsm[e] = (south ? lat_slot_of_sub<L, 1, 1>(ia) : lat_slot_of_sub<L, 1, -1>(ia)) * WPLANE + row * WX + 1 + i;
       }
@@ -266,9 +272,10 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
   const R* hptr[HPT];
 #pragma unroll
   for (int e = 0; e < HPT; ++e) hptr[e] = shc + hbase[e];
+  const bool zwrap = args.per[2] != 0;
   auto halo_fetch = [&](R(&dst)[HPT], int z) {
     const bool ok = z <= z1 && plane_needed(z);
-    const int zw = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+    const int zw = !zwrap ? z : (z < 0 ? z + nz : (z >= nz ? z - nz : z));
 #pragma unroll
     for (int e = 0; e < HPT; ++e) dst[e] = (ok && hval[e]) ? hptr[e][int64_t(zw) * hzs[e]] : R(0);
   };
@@ -285,7 +292,7 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
 
   const int wbase = (ty + PY) * WX + (tx0 + 1);  // odd; win0 is shifted by one
 
-  const int64_t nzy = int64_t(nz) * ny, nzx = int64_t(nz) * nx;
+  const int64_t nzy = int64_t(args.nzs) * ny, nzx = int64_t(args.nzs) * nx;
   if (exp_warp) {
 #pragma unroll 1
     for (int p = exp_lane; p < pcount; p += 32 * NEXW) {
@@ -295,8 +302,9 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
       const unsigned faces = (ptx == 0 && nbW ? kFaceW : 0u) | (ptx == bxa - 1 && nbE ? kFaceE : 0u) |
                              (NYF > 0 && pty == 0 && nbS ? kFaceS : 0u) |
                              (NYF > 0 && pty == bya - 1 && nbN ? kFaceN : 0u);
-      desc_off[2 * p] = args.sx_off + (int64_t(bI) * NXF) * nzy + (y0 + pty);
-      desc_off[2 * p + 1] = NYF > 0 ? args.sy_off + (int64_t(bJ) * NYF) * nzx + (x0 + ptx) : 0;
+      desc_off[2 * p] = args.sx_off + (int64_t(bI) * NXF) * nzy + int64_t(args.zg) * ny + (y0 + pty);
+      desc_off[2 * p + 1] =
+          NYF > 0 ? args.sy_off + (int64_t(bJ) * NYF) * nzx + int64_t(args.zg) * nx + (x0 + ptx) : 0;
       desc_faces[p] = faces;
     }
   }
@@ -365,7 +373,8 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
       const bool low = (c == z0 - 1);
       const int side = low ? 1 : 0;
       const int bb = low ? bKd : bKu;
-      const int64_t base = args.sz_off + (int64_t(side) * nbz + bb) * NZF * int64_t(ny) * nx + int64_t(y) * nx + x;
+      const int64_t base =
+          args.sz_off + (int64_t(side) * args.nbzs + bb + args.zg) * NZF * int64_t(ny) * nx + int64_t(y) * nx + x;
       onl[0] = onl[1] = onl[2] = V(0);
       static_for<0, Q>([&](auto A_) {
         constexpr int a = decltype(A_)::value;
@@ -479,8 +488,8 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
       bdn_mask0 = bdn_mask1 = 0;
     }
     // halfway bounce-back for destination plane g, lane by lane
-    if (real_g && act0 && (xy_wall || (z_walls && (g == 0 || g == nz - 1)))) {
-      const bool bzlo = z_walls && g == 0, bzhi = z_walls && g == nz - 1;
+    if (real_g && act0 && (xy_wall || (zwall_lo && g == 0) || (zwall_hi && g == nz - 1))) {
+      const bool bzlo = zwall_lo && g == 0, bzhi = zwall_hi && g == nz - 1;
       static_for<0, Q>([&](auto A_) {
         constexpr int a = decltype(A_)::value;
         constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);

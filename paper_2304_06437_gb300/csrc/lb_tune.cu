@@ -89,6 +89,8 @@ int lb_autotune(lb_ctx* ctx, int32_t steps, lb_tune_entry* table, int32_t cap, i
   if (!ctx || steps < 1) return LB_E_INVAL;
   if (n_entries) *n_entries = 0;
   if (ctx->scheme != LB_SCHEME_FUSED) return LB_E_UNSUPPORTED;
+  // a slab's brick cross-section must stay that of its neighbours
+  if (ctx->g.zlink[0] || ctx->g.zlink[1]) return LB_E_UNSUPPORTED;
   const TuneKey key = key_of(ctx);
   const void* best = nullptr;
   {

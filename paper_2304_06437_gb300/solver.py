@@ -53,6 +53,7 @@ class Solver:
                  rho0=1.0, force=(0.0, 0.0, 0.0), stream=None, tile=None, device=-1):
         self._lib = B.load()
         self._ctx = ctypes.c_void_p()
+        self._owned = True
         self.lattice = lattice
         self.lat_id = B.LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
         d = 2 if self.lat_id == B.LB_D2Q9 else 3
@@ -87,9 +88,27 @@ class Solver:
                                     ctypes.byref(self._ctx)), "lb_create")
 
     # ------------------------------------------------------------ lifetime
+    @classmethod
+    def _view(cls, ctx_ptr, lattice, dims, rho0=1.0):
+        """A non-owning Solver over a context that something else (a slab
+        group) owns and destroys."""
+        self = cls.__new__(cls)
+        self._lib = B.load()
+        self._ctx = ctypes.c_void_p(ctx_ptr)
+        self._owned = False
+        self.lattice = lattice
+        self.lat_id = B.LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+        self.d = 2 if self.lat_id == B.LB_D2Q9 else 3
+        self.q = {0: 9, 1: 19, 2: 27}[self.lat_id]
+        self.dims = tuple(int(v) for v in (list(dims) + [1] * 3)[:3])
+        self.n = self.dims[0] * self.dims[1] * self.dims[2]
+        self.rho0 = float(rho0)
+        return self
+
     def close(self):
         if getattr(self, "_ctx", None) and self._ctx.value:
-            self._lib.lb_destroy(self._ctx)
+            if getattr(self, "_owned", True):
+                self._lib.lb_destroy(self._ctx)
             self._ctx = ctypes.c_void_p()
 
     def __del__(self):
@@ -177,6 +196,22 @@ class Solver:
         B.check(self._lib.lb_autotune(self._ctx, int(steps), tab, cap, ctypes.byref(n)), "lb_autotune")
         return [{name: getattr(tab[i], name) for name, _ in tab[i]._fields_} for i in range(n.value)]
 
+    # ------------------------------------------------------------ slab halos
+    def halo_bytes(self) -> int:
+        n = ctypes.c_int64()
+        B.check(self._lib.lb_halo_bytes(self._ctx, ctypes.byref(n)), "lb_halo_bytes")
+        return n.value
+
+    def halo_pack(self, side, buf):
+        """Enqueue the records leaving through link face `side` (0 low, 1
+        high) into buf, a contiguous CUDA tensor of halo_bytes() bytes."""
+        B.check(self._lib.lb_halo_pack(self._ctx, int(side), ctypes.c_void_p(buf.data_ptr())), "lb_halo_pack")
+
+    def halo_unpack(self, side, buf):
+        """Enqueue the copy of a neighbour's message into the ghost records of
+        link face `side`."""
+        B.check(self._lib.lb_halo_unpack(self._ctx, int(side), ctypes.c_void_p(buf.data_ptr())), "lb_halo_unpack")
+
     def info(self) -> dict:
         inf = B.lb_info_t()
         B.check(self._lib.lb_info(self._ctx, ctypes.byref(inf)), "lb_info")
@@ -217,6 +252,106 @@ class Batch:
         if getattr(self, "_b", None) and self._b.value:
             self._lib.lb_batch_destroy(self._b)
             self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class SlabGroup:
+    """One domain cut into slabs along its slowest axis (z in 3D, y in 2D),
+    one context and stream per rank, halos exchanged on the device between
+    steps (lb_group_*): the decomposition of a multi-GPU run, in one process.
+    Initialisation and readout split or join the canonical arrays by the
+    ranks' node ranges (a slab is a contiguous range of nodes)."""
+
+    def __init__(self, lattice, dims, tau, nranks=2, counts=None, faces=None, wall_u=None, storage="f32",
+                 rho0=1.0, force=(0.0, 0.0, 0.0), tile=None, device=-1):
+        self._lib = B.load()
+        self.lattice = lattice
+        lat_id = B.LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+        self.d = 2 if lat_id == B.LB_D2Q9 else 3
+        self.q = {0: 9, 1: 19, 2: 27}[lat_id]
+        dims = list(dims) + [1] * (3 - len(dims))
+        self.dims = tuple(int(v) for v in dims[:3])
+        self.n = self.dims[0] * self.dims[1] * self.dims[2]
+        bnd = B.lb_boundary()
+        faces = faces if faces is not None else [B.LB_PERIODIC] * 6
+        for k in range(6):
+            fk = faces[k] if k < len(faces) else B.LB_PERIODIC
+            bnd.kind[k] = Solver._FACE[fk] if isinstance(fk, str) else int(fk)
+            for al in range(3):
+                bnd.wall_u[k][al] = float(wall_u[k][al]) if wall_u is not None else 0.0
+        opt = B.lb_options()
+        self._lib.lb_default_options(ctypes.byref(opt))
+        opt.storage = B.STORAGES[storage] if isinstance(storage, str) else int(storage)
+        opt.rho0 = float(rho0)
+        for k in range(3):
+            opt.force[k] = float(force[k]) if k < len(force) else 0.0
+        if tile is not None:
+            for k in range(3):
+                opt.tile[k] = int(tile[k]) if k < len(tile) else 0
+        opt.device = int(device)
+        cnt = (ctypes.c_int64 * nranks)(*counts) if counts is not None else None
+        self._g = ctypes.c_void_p()
+        B.check(self._lib.lb_group_create(lat_id, (ctypes.c_int64 * 3)(*self.dims), float(tau), ctypes.byref(bnd),
+                                          ctypes.byref(opt), int(nranks), cnt, ctypes.byref(self._g)),
+                "lb_group_create")
+        slow = self.d - 1
+        plane = self.n // self.dims[slow]  # nodes per plane of the slowest axis
+        self.ranks, self.ranges = [], []
+        for r in range(nranks):
+            c = ctypes.c_void_p()
+            off = ctypes.c_int64()
+            B.check(self._lib.lb_group_rank(self._g, r, ctypes.byref(c), ctypes.byref(off)), "lb_group_rank")
+            rd = list(self.dims)
+            rd[slow] = (counts[r] if counts is not None else
+                        self.dims[slow] // nranks + (1 if r < self.dims[slow] % nranks else 0))
+            self.ranks.append(Solver._view(c.value, lattice, rd, rho0))
+            self.ranges.append((off.value * plane, (off.value + rd[slow]) * plane))
+
+    def _split(self, a, comps):
+        a = np.asarray(a, dtype=np.float64).reshape(comps, self.n)
+        return [np.ascontiguousarray(a[:, n0:n1]) for n0, n1 in self.ranges]
+
+    def set_populations(self, f):
+        for s, part in zip(self.ranks, self._split(f, self.q)):
+            s.set_populations(part)
+
+    def get_populations(self):
+        return np.concatenate([s.get_populations() for s in self.ranks], axis=1)
+
+    def init_moments(self, rho, u, pineq=None):
+        np_ = 3 if self.d == 2 else 6
+        rs, us = self._split(rho, 1), self._split(u, self.d)
+        ps = self._split(pineq, np_) if pineq is not None else [None] * len(self.ranks)
+        for s, r, uu, p in zip(self.ranks, rs, us, ps):
+            s.init_moments(np.ascontiguousarray(r[0]), uu, p)
+
+    def moments(self):
+        parts = [s.moments() for s in self.ranks]
+        return np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts], axis=1)
+
+    def step(self, n=1):
+        B.check(self._lib.lb_group_step(self._g, int(n)), "lb_group_step")
+
+    def sync(self):
+        B.check(self._lib.lb_group_sync(self._g), "lb_group_sync")
+
+    def close(self):
+        if getattr(self, "_g", None) and self._g.value:
+            for s in self.ranks:
+                s.close()
+            self._lib.lb_group_destroy(self._g)
+            self._g = ctypes.c_void_p()
 
     def __del__(self):
         try:

@@ -65,6 +65,48 @@ def test_create_rejects_bad_arguments_without_a_device(lib):
     assert lib.lb_sync(None) == B.LB_E_INVAL
 
 
+def test_slab_calls_reject_bad_arguments_without_a_device(lib):
+    ctx = ctypes.c_void_p()
+    dims = (ctypes.c_int64 * 3)(8, 8, 8)
+    opt = B.lb_options()
+    lib.lb_default_options(ctypes.byref(opt))
+    link_x = B.lb_boundary()
+    link_x.kind[0] = link_x.kind[1] = B.LB_LINK  # link faces only on the slowest axis
+    assert lib.lb_create(B.LB_D3Q19, dims, 0.8, ctypes.byref(link_x), ctypes.byref(opt), ctypes.byref(ctx)) == \
+        B.LB_E_INVAL
+    link_z = B.lb_boundary()
+    link_z.kind[4] = link_z.kind[5] = B.LB_LINK
+    bad_kind = B.lb_boundary()
+    bad_kind.kind[4] = bad_kind.kind[5] = 4
+    assert lib.lb_create(B.LB_D3Q19, dims, 0.8, ctypes.byref(bad_kind), ctypes.byref(opt), ctypes.byref(ctx)) == \
+        B.LB_E_INVAL
+    opt.scheme = B.LB_SCHEME_TWO_PASS
+    assert lib.lb_create(B.LB_D3Q19, dims, 0.8, ctypes.byref(link_z), ctypes.byref(opt), ctypes.byref(ctx)) == \
+        B.LB_E_UNSUPPORTED
+    lib.lb_default_options(ctypes.byref(opt))
+    grp = ctypes.c_void_p()
+    # a group places the links itself; counts must cover the slowest axis
+    assert lib.lb_group_create(B.LB_D3Q19, dims, 0.8, ctypes.byref(link_z), ctypes.byref(opt), 2, None,
+                               ctypes.byref(grp)) == B.LB_E_INVAL
+    assert lib.lb_group_create(B.LB_D3Q19, dims, 0.8, None, ctypes.byref(opt), 9, None, ctypes.byref(grp)) == \
+        B.LB_E_INVAL
+    assert lib.lb_group_create(B.LB_D3Q19, dims, 0.8, None, ctypes.byref(opt), 2, (ctypes.c_int64 * 2)(3, 4),
+                               ctypes.byref(grp)) == B.LB_E_INVAL
+    assert lib.lb_group_create(B.LB_D3Q19, dims, 0.8, None, ctypes.byref(opt), 2, (ctypes.c_int64 * 2)(8, 0),
+                               ctypes.byref(grp)) == B.LB_E_INVAL
+    opt.scheme = B.LB_SCHEME_TWO_PASS
+    assert lib.lb_group_create(B.LB_D3Q19, dims, 0.8, None, ctypes.byref(opt), 2, None, ctypes.byref(grp)) == \
+        B.LB_E_UNSUPPORTED
+    n = ctypes.c_int64()
+    assert lib.lb_halo_bytes(None, ctypes.byref(n)) == B.LB_E_INVAL
+    assert lib.lb_halo_pack(None, 0, None) == B.LB_E_INVAL
+    assert lib.lb_halo_unpack(None, 1, None) == B.LB_E_INVAL
+    assert lib.lb_group_step(None, 1) == B.LB_E_INVAL
+    assert lib.lb_group_sync(None) == B.LB_E_INVAL
+    assert lib.lb_group_rank(None, 0, None, None) == B.LB_E_INVAL
+    lib.lb_group_destroy(None)
+
+
 @pytest.mark.parametrize("lat", ["D2Q9", "D3Q19", "D3Q27"])
 def test_lattice_table_matches_oracle(lat):
     c, w, opp = lattice_table(lat)

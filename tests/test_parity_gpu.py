@@ -228,11 +228,14 @@ def _numpy_reductions(lat, cfg, f, f_prev, force, rho0=1.0):
 @pytest.mark.parametrize("lat", LATTICES)
 @pytest.mark.parametrize("case", ["periodic_forced_flow", "lid"])
 @pytest.mark.parametrize("storage", ["f64", "f32"])
-def test_reductions_match_numpy_sums_of_oracle_states(Solver, lat, case, storage):
-    """lb_reduce (S6) against numpy sums over two oracle states t and t + K:
-    a mean flow (or a driven lid) makes the momentum non-zero and changing,
-    so a wrong or constant value fails; the residual is compared with the
-    definition ||u_t+K - u_t|| / ||u_t+K||."""
+def test_reductions_match_numpy_sums(Solver, lat, case, storage):
+    """lb_reduce (S6) against numpy sums of the definitions (section 2's
+    moments; u = (j + F/2)/rho0): at an oracle state t set from outside, and
+    K steps later at the state the GPU reached, read back through
+    lb_get_populations -- which the oracle's own state at t + K pins within
+    the parity tolerance.  A mean flow (or a driven lid) makes the momentum
+    non-zero and changing, so a wrong or constant value fails; the residual is
+    compared with ||u_t+K - u_t|| / ||u_t+K||."""
     d = dim_of(lat)
     dims = (40, 28, 1) if d == 2 else (17, 13, 11)
     if case == "lid":
@@ -244,21 +247,25 @@ def test_reductions_match_numpy_sums_of_oracle_states(Solver, lat, case, storage
     cfg = oracle_cfg(lat, dims, 0.62, faces, wall_u, force=force)
     rho, u, pineq = synth.smooth_random_state(dims, d, seed=17)
     u = u + np.array([0.02, -0.013, 0.007][:d])[:, None]
+    K = 20
     f_a = oracle.run(cfg, oracle.init(cfg, rho, np.ascontiguousarray(u), pineq), 5)
-    f_b = oracle.run(cfg, f_a, 20)
-    # the states as stored (FP32 storage rounds each shifted population): the
+    f_b_oracle = oracle.run(cfg, f_a, K)
+    # the state as stored (FP32 storage rounds each shifted population): the
     # reductions read the stored values, so the numpy sums take the same ones
     w = oracle.lattice_tables(lat)[1]
     f_a = round_populations(f_a, w, storage)
-    f_b = round_populations(f_b, w, storage)
     s = Solver(lat, dims, 0.62, faces=faces, wall_u=wall_u, storage=storage, force=force)
     s.set_populations(np.ascontiguousarray(f_a))
     first = s.reduce(residual=True)
-    s.set_populations(np.ascontiguousarray(f_b))
+    s.step(K)
     got = s.reduce(residual=True)
+    f_b = s.get_populations()
     s.close()
+    # the GPU's state at t + K is the oracle's (parity tolerance per population)
+    assert np.abs(f_b - f_b_oracle).max() <= {"f64": 1e-13, "f32": 2e-6}[storage]
     want_a = _numpy_reductions(lat, cfg, f_a, f_a, force)
     want = _numpy_reductions(lat, cfg, f_b, f_a, force)
+    want_oracle = _numpy_reductions(lat, cfg, f_b_oracle, f_a, force)
     # the first residual has no previous velocity: 1 by definition
     assert first["residual"] == 1.0
     # FP64 sums of the same stored values: rounding order only
@@ -278,6 +285,24 @@ def test_reductions_match_numpy_sums_of_oracle_states(Solver, lat, case, storage
     rtol = 1e-10
     assert abs(r - want["residual_f32prev"]) <= rtol * want["residual"]
     assert abs(r - want["residual"]) <= 2.0 ** -24 * want["upnorm"] / want["unorm"] + rtol * want["residual"]
+    # and against the oracle's own state at t + K (FP64: to rounding; FP32:
+    # the per-population error of at most 2e-6 moves u by ~1e-6 relative)
+    assert abs(r - want_oracle["residual"]) <= {"f64": 1e-9, "f32": 1e-3}[storage] * want_oracle["residual"]
+
+
+def test_residual_restarts_after_a_state_change(Solver):
+    """Setting the state from outside starts a new residual history: the next
+    residual call reports 1 (no previous velocity of this history)."""
+    dims = (12, 10, 8)
+    rho, u, pineq = synth.smooth_random_state(dims, 3, seed=4)
+    s = Solver("D3Q19", dims, 0.7, storage="f64")
+    s.init_moments(rho, np.ascontiguousarray(u), np.ascontiguousarray(pineq))
+    assert s.reduce(residual=True)["residual"] == 1.0
+    s.step(3)
+    assert 0.0 < s.reduce(residual=True)["residual"] < 1.0
+    s.set_populations(s.get_populations())
+    assert s.reduce(residual=True)["residual"] == 1.0
+    s.close()
 
 
 def test_init_moments_device_buffers_and_readback(Solver):
