@@ -59,6 +59,10 @@ struct K1Args {
   // planes per x / y record, nbzs = nbz + 2 zg brick rows per z-record side.
   int zlink[2];
   int zg, nzs, nbzs;
+  // per-plane tests read from the parameter bank (no registers in the
+  // sweep): the plane of a wall at the -z / +z face (0 / nz - 1; -1 where
+  // that face is periodic or a link), and nz where z wraps (periodic), else 0
+  int zwl, zwh, zwrap;
   int bz, nbx, nby, nbz;
   void* f;
   const R* sh_cur;
@@ -233,7 +237,7 @@ __device__ __forceinline__ void export_face(const Coef<R>& kc, ShellSpot<R> s) {
 
 // Collide the completed (rounded) state of one node once more and export the
 // populations that leave the brick through the flagged faces.
-template <class L, class S, class R, bool FORCE>
+template <class L, class S, class R, bool FORCE, bool LINK = false>
 __device__ __forceinline__ void export_node(const K1Args<R>& args, const R (&fin)[L::Q], int x, int y, int zd,
                                             unsigned faces, int bI, int bJ, int bK) {
   constexpr int NXF = count_dirs<L>(0, 1), NYF = count_dirs<L>(1, 1), NZF = count_dirs<L>(2, 1);
@@ -247,11 +251,14 @@ __device__ __forceinline__ void export_node(const K1Args<R>& args, const R (&fin
   Coef<R> kc;
   coeffs<L, R, FORCE>(m, args.ph, kc);
   R* shn = args.sh_next;
-  const int64_t nzy = int64_t(args.nzs) * args.ny, nzx = int64_t(args.nzs) * args.nx;
+  // LINK: the shell of a slab context, with ghost planes / brick rows
+  const int zg = LINK ? args.zg : 0;
+  const int64_t nzy = int64_t(LINK ? args.nzs : args.nz) * args.ny;
+  const int64_t nzx = int64_t(LINK ? args.nzs : args.nz) * args.nx;
   const int64_t nyx = int64_t(args.ny) * args.nx;
   if (faces & (kFaceW | kFaceE)) {
     // SX[side][I][ia][z + zg][y]
-    const int64_t row = int64_t(zd + args.zg) * args.ny + y;
+    const int64_t row = int64_t(zd + zg) * args.ny + y;
     if (faces & kFaceW)
       export_face<L, R, 0, -1>(kc, {shn + args.sx_off + (int64_t(bI) * NXF) * nzy + row, nzy});
     if (faces & kFaceE)
@@ -260,7 +267,7 @@ __device__ __forceinline__ void export_node(const K1Args<R>& args, const R (&fin
   if constexpr (NYF > 0) {
     if (faces & (kFaceS | kFaceN)) {
       // SY[side][J][ia][z + zg][x]
-      const int64_t row = int64_t(zd + args.zg) * args.nx + x;
+      const int64_t row = int64_t(zd + zg) * args.nx + x;
       if (faces & kFaceS)
         export_face<L, R, 1, -1>(kc, {shn + args.sy_off + (int64_t(bJ) * NYF) * nzx + row, nzx});
       if (faces & kFaceN)
@@ -271,9 +278,10 @@ __device__ __forceinline__ void export_node(const K1Args<R>& args, const R (&fin
     // SZ[side][K + zg][ia][y][x]
     const int64_t row = int64_t(y) * args.nx + x;
     if (faces & kFaceD)
-      export_face<L, R, 2, -1>(kc, {shn + args.sz_off + (int64_t(bK + args.zg) * NZF) * nyx + row, nyx});
+      export_face<L, R, 2, -1>(kc, {shn + args.sz_off + (int64_t(bK + zg) * NZF) * nyx + row, nyx});
     if (faces & kFaceU)
-      export_face<L, R, 2, 1>(kc, {shn + args.sz_off + ((int64_t(args.nbzs) + bK + args.zg) * NZF) * nyx + row, nyx});
+      export_face<L, R, 2, 1>(
+          kc, {shn + args.sz_off + ((int64_t(LINK ? args.nbzs : args.nbz) + bK + zg) * NZF) * nyx + row, nyx});
   }
 }
 
@@ -318,7 +326,11 @@ __device__ __forceinline__ void export_one_face(const K1Args<R>& args, const R (
 // Returns false if a TMA wait timed out (the CTA recorded LB_E_TIMEOUT and
 // must stop).  On return every copy the brick issued has completed and the
 // mbarriers are invalidated, so the CTA may start another brick.
-template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE, int TS = 0>
+//
+// LINK: compiled for contexts with a link face (slab decomposition); the
+// other instantiations compile the plain form, whose shell has no ghosts.
+template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE, int TS = 0,
+          bool LINK = false>
 __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args<R>& args, const int bI,
                                          const int bJ, const int bK) {
   using Sh = K1Shape<L, S, R, BX, BY, NS, WB, NXW, TS>;
@@ -363,13 +375,17 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   const bool nbE = x0 + bxa < nx || args.per[0];
   const bool nbS = y0 > 0 || args.per[1];
   const bool nbN = y0 + bya < ny || args.per[1];
-  const bool nbD = z0 > 0 || args.per[2] || args.zlink[0];
-  const bool nbU = z1 < nz || args.per[2] || args.zlink[1];
+  const bool nbD = z0 > 0 || args.per[2] || (LINK && args.zlink[0]);
+  const bool nbU = z1 < nz || args.per[2] || (LINK && args.zlink[1]);
   const int bIw = (bI + nbx - 1) % nbx, bIe = (bI + 1) % nbx;
   const int bJs = (bJ + nby - 1) % nby, bJn = (bJ + 1) % nby;
   // the brick rows below / above (a link face's ghost row is -1 / nbz)
-  const int bKd = args.per[2] ? (bK + nbz - 1) % nbz : bK - 1;
-  const int bKu = args.per[2] ? (bK + 1) % nbz : bK + 1;
+  const int bKd = (LINK && !args.per[2]) ? bK - 1 : (bK + nbz - 1) % nbz;
+  const int bKu = (LINK && !args.per[2]) ? bK + 1 : (bK + 1) % nbz;
+  // shell planes per x / y record and brick rows per z-record side
+  const int nzs = LINK ? args.nzs : nz;
+  const int nbzs = LINK ? args.nbzs : nbz;
+  const int zg = LINK ? args.zg : 0;
 
   // bounce-back predicates of this node along x and y: the upstream point of
   // a direction with c = +1 is x - 1, which leaves a non-periodic low face at x = 0
@@ -378,9 +394,7 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   const bool bylo = active && (y == 0) && !args.per[1];
   const bool byhi = active && (y == ny - 1) && !args.per[1];
   const bool xy_wall = bxlo || bxhi || bylo || byhi;
-  // walls at the z faces (neither periodic nor a link to another slab)
-  const bool zwall_lo = !args.per[2] && !args.zlink[0];
-  const bool zwall_hi = !args.per[2] && !args.zlink[1];
+  const bool z_walls = !args.per[2];
 
   S* __restrict__ fglob = static_cast<S*>(args.f);
   const R* __restrict__ shc = args.sh_cur;
@@ -459,8 +473,7 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
         const int side = west ? 1 : 0;
         const int bb = west ? bIw : bIe;
         hval[e] = ok;
-        hbase[e] = args.sx_off + ((int64_t(side) * nbx + bb) * NXF + ia) * int64_t(args.nzs) * ny +
-                   int64_t(args.zg) * ny + sy;
+        hbase[e] = args.sx_off + ((int64_t(side) * nbx + bb) * NXF + ia) * int64_t(nzs) * ny + int64_t(zg) * ny + sy;
         hzs[e] = ny;
         hsm[e] = (west ? lat_slot_of_sub<L, 0, 1>(ia) : lat_slot_of_sub<L, 0, -1>(ia)) * WPLANE + r * WX + col;
       } else {
@@ -474,8 +487,7 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
         const int side = south ? 1 : 0;
         const int bb = south ? bJs : bJn;
         hval[e] = ok;
-        hbase[e] = args.sy_off + ((int64_t(side) * nby + bb) * NYF + ia) * int64_t(args.nzs) * nx +
-                   int64_t(args.zg) * nx + x0 + i;
+        hbase[e] = args.sy_off + ((int64_t(side) * nby + bb) * NYF + ia) * int64_t(nzs) * nx + int64_t(zg) * nx + x0 + i;
         hzs[e] = nx;
         hsm[e] = (south ? lat_slot_of_sub<L, 1, 1>(ia) : lat_slot_of_sub<L, 1, -1>(ia)) * WPLANE + row * WX + 1 + i;
       }
@@ -504,10 +516,10 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
       if (!hval[e]) hsm[e] = -1;
     }
   }
-  const bool zwrap = args.per[2] != 0;
   auto halo_fetch = [&](R(&dst)[HPT], int z) {
     const bool ok = z <= z1 && plane_needed(z);
-    const int zw = !zwrap ? z : (z < 0 ? z + nz : (z >= nz ? z - nz : z));
+    const int zw = LINK ? (z < 0 ? z + args.zwrap : (z >= nz ? z - args.zwrap : z))
+                        : (z < 0 ? z + nz : (z >= nz ? z - nz : z));
 #pragma unroll
     for (int e = 0; e < HPT; ++e) {
       if constexpr (Sh::HSMEM) {
@@ -535,7 +547,7 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
 
   // export of the staged lateral perimeter of plane zx (whole warps)
   // resolve each perimeter node's shell records once per brick
-  const int64_t nzy = int64_t(args.nzs) * ny, nzx = int64_t(args.nzs) * nx;
+  const int64_t nzy = int64_t(nzs) * ny, nzx = int64_t(nzs) * nx;
   if (exp_warp) {
 #pragma unroll 1
     for (int e = exp_lane; e < PE; e += 32 * Sh::NEXW) {
@@ -548,10 +560,10 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
       const bool ok = nb && (xface ? pty < bya : ptx < bxa) && k < (xface ? Sh::SEGY : Sh::SEGX);
       // SX[side][I][ia][z][y], SY[side][J][ia][z][x]; the high face (E, N)
       // is the side-1 record, a brick-uniform distance further
-      desc_off[e] = xface ? args.sx_off + ((int64_t(face == 1 ? nbx : 0) + bI) * NXF) * nzy +
-                                int64_t(args.zg) * ny + (y0 + pty)
-                          : args.sy_off + ((int64_t(face == 3 ? nby : 0) + bJ) * NYF) * nzx +
-                                int64_t(args.zg) * nx + (x0 + ptx);
+      desc_off[e] = xface ? args.sx_off + ((int64_t(face == 1 ? nbx : 0) + bI) * NXF) * nzy + int64_t(zg) * ny +
+                                (y0 + pty)
+                          : args.sy_off + ((int64_t(face == 3 ? nby : 0) + bJ) * NYF) * nzx + int64_t(zg) * nx +
+                                (x0 + ptx);
       desc_p[e] = ok ? perimeter_index<NYF>(ptx, pty, bxa, bya) : -1;
     }
   }
@@ -610,7 +622,7 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
       const int side = low ? 1 : 0;
       const int bb = low ? bKd : bKu;
       const int64_t base =
-          args.sz_off + (int64_t(side) * args.nbzs + bb + args.zg) * NZF * int64_t(ny) * nx + int64_t(y) * nx + x;
+          args.sz_off + (int64_t(side) * nbzs + bb + zg) * NZF * int64_t(ny) * nx + int64_t(y) * nx + x;
       onl[0] = onl[1] = onl[2] = R(0);
       static_for<0, Q>([&](auto A_) {
         constexpr int a = decltype(A_)::value;
@@ -746,8 +758,10 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
         bdn_mask = 0;
       }
       // halfway bounce-back for destination plane g (threads next to a wall)
-      if (real_g && active && (xy_wall || (zwall_lo && g == 0) || (zwall_hi && g == nz - 1))) {
-        const bool bzlo = zwall_lo && g == 0, bzhi = zwall_hi && g == nz - 1;
+      if (real_g && active &&
+          (xy_wall || (LINK ? (g == args.zwl || g == args.zwh) : (z_walls && (g == 0 || g == nz - 1))))) {
+        const bool bzlo = LINK ? g == args.zwl : z_walls && g == 0;
+        const bool bzhi = LINK ? g == args.zwh : z_walls && g == nz - 1;
         static_for<0, Q>([&](auto A_) {
           constexpr int a = decltype(A_)::value;
           constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
@@ -817,7 +831,8 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
           }
         }
         const bool eD = zd == z0 && nbD, eU = zd == z1 - 1 && nbU;
-        if (eD || eU) export_node<L, S, R, FORCE>(args, G0, x, y, zd, (eD ? kFaceD : 0u) | (eU ? kFaceU : 0u), bI, bJ, bK);
+        if (eD || eU)
+          export_node<L, S, R, FORCE, LINK>(args, G0, x, y, zd, (eD ? kFaceD : 0u) | (eU ? kFaceU : 0u), bI, bJ, bK);
       }
       // every node thread (staging or not) marks the staged plane ready
       if (DEC && zd >= z0 && zd < z1) mbar_arrive(&sfull[(zd - z0) % SR]);
@@ -888,12 +903,14 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
 }
 
 // One launch per time step of one domain: one CTA per brick column.
-template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE, int TS = 0>
+template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE, int TS = 0,
+          bool LINK = false>
 __global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
     k1_fused_step(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ K1Args<R> args) {
   const int nbx = args.nbx, nby = args.nby;
   const int b = blockIdx.x;
-  k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE, TS>(&tmap, args, b % nbx, (b / nbx) % nby, b / (nbx * nby));
+  k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE, TS, LINK>(&tmap, args, b % nbx, (b / nbx) % nby,
+                                                          b / (nbx * nby));
 }
 
 // One launch per time step of many domains (a batch): a persistent grid whose
@@ -946,7 +963,7 @@ __global__ void __launch_bounds__(256) k1_bootstrap(const __grid_constant__ K1Ar
     });
     const unsigned faces = (eW ? kFaceW : 0u) | (eE ? kFaceE : 0u) | (eS ? kFaceS : 0u) | (eN ? kFaceN : 0u) |
                            (eD ? kFaceD : 0u) | (eU ? kFaceU : 0u);
-    export_node<L, S, R, FORCE>(args, fr, x, y, z, faces, bI, bJ, bK);
+    export_node<L, S, R, FORCE, true>(args, fr, x, y, z, faces, bI, bJ, bK);
   }
 }
 

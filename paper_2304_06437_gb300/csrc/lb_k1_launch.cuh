@@ -56,6 +56,9 @@ K1Args<R> k1_make_args(lb_ctx* ctx, int cur_parity, int next_parity) {
   a.zg = p.zg;
   a.nzs = g.nz + 2 * p.zg;
   a.nbzs = p.nbz + 2 * p.zg;
+  a.zwl = (!g.per[2] && !g.zlink[0]) ? 0 : -1;
+  a.zwh = (!g.per[2] && !g.zlink[1]) ? g.nz - 1 : -1;
+  a.zwrap = g.per[2] ? g.nz : 0;
   a.bz = p.bz;
   a.nbx = p.nbx;
   a.nby = p.nby;
@@ -78,21 +81,37 @@ struct K1Impl {
   using Sh = K1Shape<L, S, R, BX, BY, NS, WB, NXW, TS>;
 
   static cudaError_t configure() {
+    const int sm = int(Sh::SMEM);
     cudaError_t e = cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false, TS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::SMEM));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true, TS>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::SMEM));
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true, TS>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false, TS, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true, TS, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    return e;
   }
 
   static cudaError_t step(lb_ctx* ctx) {
     K1Args<R> a = k1_make_args<R>(ctx, ctx->parity, 1 - ctx->parity);
     make_bounce_terms<L, R>(ctx->g, a.bb);
     const int grid = ctx->plan.nbx * ctx->plan.nby * ctx->plan.nbz;
-    if (ctx->g.has_force)
-      k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true, TS><<<grid, Sh::NT, Sh::SMEM, ctx->stream>>>(ctx->tmap, a);
-    else
-      k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false, TS><<<grid, Sh::NT, Sh::SMEM, ctx->stream>>>(ctx->tmap, a);
+    const bool link = ctx->g.zlink[0] || ctx->g.zlink[1];
+    cudaStream_t st = ctx->stream;
+    if (link) {
+      if (ctx->g.has_force)
+        k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true, TS, true><<<grid, Sh::NT, Sh::SMEM, st>>>(ctx->tmap, a);
+      else
+        k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false, TS, true><<<grid, Sh::NT, Sh::SMEM, st>>>(ctx->tmap, a);
+    } else if (ctx->g.has_force) {
+      k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true, TS><<<grid, Sh::NT, Sh::SMEM, st>>>(ctx->tmap, a);
+    } else {
+      k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false, TS><<<grid, Sh::NT, Sh::SMEM, st>>>(ctx->tmap, a);
+    }
     return cudaGetLastError();
   }
 

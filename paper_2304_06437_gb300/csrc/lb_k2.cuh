@@ -105,7 +105,9 @@ __device__ __forceinline__ void export_lateral_pair(const K1Args<float>& args, c
 // Returns false if a TMA wait timed out (the CTA recorded LB_E_TIMEOUT and
 // must stop).  On return every copy the brick issued has completed and the
 // mbarriers are invalidated, so the CTA may start another brick.
-template <class L, class S, int BX, int BY, int NS, bool FORCE, bool UNROLL3 = false>
+// LINK: compiled for contexts with a link face (slab decomposition); the
+// other instantiations compile the plain form, whose shell has no ghosts.
+template <class L, class S, int BX, int BY, int NS, bool FORCE, bool UNROLL3 = false, bool LINK = false>
 __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args<float>& args, const int bI,
                                          const int bJ, const int bK) {
   using R = float;
@@ -169,13 +171,17 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
   const bool nbE = x0 + bxa < nx || args.per[0];
   const bool nbS = y0 > 0 || args.per[1];
   const bool nbN = y0 + bya < ny || args.per[1];
-  const bool nbD = z0 > 0 || args.per[2] || args.zlink[0];
-  const bool nbU = z1 < nz || args.per[2] || args.zlink[1];
+  const bool nbD = z0 > 0 || args.per[2] || (LINK && args.zlink[0]);
+  const bool nbU = z1 < nz || args.per[2] || (LINK && args.zlink[1]);
   const int bIw = (bI + nbx - 1) % nbx, bIe = (bI + 1) % nbx;
   const int bJs = (bJ + nby - 1) % nby, bJn = (bJ + 1) % nby;
   // the brick rows below / above (a link face's ghost row is -1 / nbz)
-  const int bKd = args.per[2] ? (bK + nbz - 1) % nbz : bK - 1;
-  const int bKu = args.per[2] ? (bK + 1) % nbz : bK + 1;
+  const int bKd = (LINK && !args.per[2]) ? bK - 1 : (bK + nbz - 1) % nbz;
+  const int bKu = (LINK && !args.per[2]) ? bK + 1 : (bK + 1) % nbz;
+  // shell planes per x / y record and brick rows per z-record side
+  const int nzs = LINK ? args.nzs : nz;
+  const int nbzs = LINK ? args.nbzs : nbz;
+  const int zg = LINK ? args.zg : 0;
 
   // bounce-back predicates per lane (x is even, so only lane .x can sit on x = 0)
   const bool bxlo0 = act0 && (x == 0) && !args.per[0];
@@ -184,9 +190,7 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
   const bool bylo = act0 && (y == 0) && !args.per[1];
   const bool byhi = act0 && (y == ny - 1) && !args.per[1];
   const bool xy_wall = bxlo0 || bxhi0 || bxhi1 || bylo || byhi;
-  // walls at the z faces (neither periodic nor a link to another slab)
-  const bool zwall_lo = !args.per[2] && !args.zlink[0];
-  const bool zwall_hi = !args.per[2] && !args.zlink[1];
+  const bool z_walls = !args.per[2];
 
   S* __restrict__ fglob = static_cast<S*>(args.f);
   const R* __restrict__ shc = args.sh_cur;
@@ -238,8 +242,7 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
         const int side = west ? 1 : 0;
         const int bb = west ? bIw : bIe;
         hval[e] = ok;
-        hbase[e] = args.sx_off + ((int64_t(side) * nbx + bb) * NXF + ia) * int64_t(args.nzs) * ny +
-                   int64_t(args.zg) * ny + sy;
+        hbase[e] = args.sx_off + ((int64_t(side) * nbx + bb) * NXF + ia) * int64_t(nzs) * ny + int64_t(zg) * ny + sy;
         hzs[e] = ny;
         hsm[e] = (west ? lat_slot_of_sub<L, 0, 1>(ia) : lat_slot_of_sub<L, 0, -1>(ia)) * WPLANE + r * WX + col;
       } else {
@@ -253,8 +256,7 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
         const int side = south ? 1 : 0;
         const int bb = south ? bJs : bJn;
         hval[e] = ok;
-        hbase[e] = args.sy_off + ((int64_t(side) * nby + bb) * NYF + ia) * int64_t(args.nzs) * nx +
-                   int64_t(args.zg) * nx + x0 + i;
+        hbase[e] = args.sy_off + ((int64_t(side) * nby + bb) * NYF + ia) * int64_t(nzs) * nx + int64_t(zg) * nx + x0 + i;
         hzs[e] = nx;
         hsm[e] = (south ? lat_slot_of_sub<L, 1, 1>(ia) : lat_slot_of_sub<L, 1, -1>(ia)) * WPLANE + row * WX + 1 + i;
       }
@@ -272,10 +274,10 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
   const R* hptr[HPT];
 #pragma unroll
   for (int e = 0; e < HPT; ++e) hptr[e] = shc + hbase[e];
-  const bool zwrap = args.per[2] != 0;
   auto halo_fetch = [&](R(&dst)[HPT], int z) {
     const bool ok = z <= z1 && plane_needed(z);
-    const int zw = !zwrap ? z : (z < 0 ? z + nz : (z >= nz ? z - nz : z));
+    const int zw = LINK ? (z < 0 ? z + args.zwrap : (z >= nz ? z - args.zwrap : z))
+                        : (z < 0 ? z + nz : (z >= nz ? z - nz : z));
 #pragma unroll
     for (int e = 0; e < HPT; ++e) dst[e] = (ok && hval[e]) ? hptr[e][int64_t(zw) * hzs[e]] : R(0);
   };
@@ -292,7 +294,7 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
 
   const int wbase = (ty + PY) * WX + (tx0 + 1);  // odd; win0 is shifted by one
 
-  const int64_t nzy = int64_t(args.nzs) * ny, nzx = int64_t(args.nzs) * nx;
+  const int64_t nzy = int64_t(nzs) * ny, nzx = int64_t(nzs) * nx;
   if (exp_warp) {
 #pragma unroll 1
     for (int p = exp_lane; p < pcount; p += 32 * NEXW) {
@@ -302,9 +304,8 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
       const unsigned faces = (ptx == 0 && nbW ? kFaceW : 0u) | (ptx == bxa - 1 && nbE ? kFaceE : 0u) |
                              (NYF > 0 && pty == 0 && nbS ? kFaceS : 0u) |
                              (NYF > 0 && pty == bya - 1 && nbN ? kFaceN : 0u);
-      desc_off[2 * p] = args.sx_off + (int64_t(bI) * NXF) * nzy + int64_t(args.zg) * ny + (y0 + pty);
-      desc_off[2 * p + 1] =
-          NYF > 0 ? args.sy_off + (int64_t(bJ) * NYF) * nzx + int64_t(args.zg) * nx + (x0 + ptx) : 0;
+      desc_off[2 * p] = args.sx_off + (int64_t(bI) * NXF) * nzy + int64_t(zg) * ny + (y0 + pty);
+      desc_off[2 * p + 1] = NYF > 0 ? args.sy_off + (int64_t(bJ) * NYF) * nzx + int64_t(zg) * nx + (x0 + ptx) : 0;
       desc_faces[p] = faces;
     }
   }
@@ -374,7 +375,7 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
       const int side = low ? 1 : 0;
       const int bb = low ? bKd : bKu;
       const int64_t base =
-          args.sz_off + (int64_t(side) * args.nbzs + bb + args.zg) * NZF * int64_t(ny) * nx + int64_t(y) * nx + x;
+          args.sz_off + (int64_t(side) * nbzs + bb + zg) * NZF * int64_t(ny) * nx + int64_t(y) * nx + x;
       onl[0] = onl[1] = onl[2] = V(0);
       static_for<0, Q>([&](auto A_) {
         constexpr int a = decltype(A_)::value;
@@ -488,8 +489,10 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
       bdn_mask0 = bdn_mask1 = 0;
     }
     // halfway bounce-back for destination plane g, lane by lane
-    if (real_g && act0 && (xy_wall || (zwall_lo && g == 0) || (zwall_hi && g == nz - 1))) {
-      const bool bzlo = zwall_lo && g == 0, bzhi = zwall_hi && g == nz - 1;
+    if (real_g && act0 &&
+        (xy_wall || (LINK ? (g == args.zwl || g == args.zwh) : (z_walls && (g == 0 || g == nz - 1))))) {
+      const bool bzlo = LINK ? g == args.zwl : z_walls && g == 0;
+      const bool bzhi = LINK ? g == args.zwh : z_walls && g == nz - 1;
       static_for<0, Q>([&](auto A_) {
         constexpr int a = decltype(A_)::value;
         constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
@@ -585,11 +588,11 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
         R fs[Q];
 #pragma unroll
         for (int a = 0; a < Q; ++a) fs[a] = G0[a].x;
-        export_node<L, S, R, FORCE>(args, fs, x, y, zd, fz, bI, bJ, bK);
+        export_node<L, S, R, FORCE, LINK>(args, fs, x, y, zd, fz, bI, bJ, bK);
         if (act1) {
 #pragma unroll
           for (int a = 0; a < Q; ++a) fs[a] = G0[a].y;
-          export_node<L, S, R, FORCE>(args, fs, x + 1, y, zd, fz, bI, bJ, bK);
+          export_node<L, S, R, FORCE, LINK>(args, fs, x + 1, y, zd, fz, bI, bJ, bK);
         }
       }
     }
@@ -645,12 +648,12 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
 // One launch per time step of one domain: one CTA per brick column.  D2Q9
 // sweeps three planes per loop trip and keeps three CTAs per SM (the register
 // cap that this implies holds the unrolled body without spills).
-template <class L, class S, int BX, int BY, int NS, bool FORCE>
+template <class L, class S, int BX, int BY, int NS, bool FORCE, bool LINK = false>
 __global__ void __launch_bounds__(BX* BY / 2, (L::Q == 9 ? 3 : 1))
     k2_fused_step(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ K1Args<float> args) {
   const int nbx = args.nbx, nby = args.nby;
   const int b = blockIdx.x;
-  k2_brick<L, S, BX, BY, NS, FORCE, L::Q == 9>(&tmap, args, b % nbx, (b / nbx) % nby, b / (nbx * nby));
+  k2_brick<L, S, BX, BY, NS, FORCE, L::Q == 9, LINK>(&tmap, args, b % nbx, (b / nbx) % nby, b / (nbx * nby));
 }
 
 // One launch per time step of many domains (a batch): a persistent grid whose
@@ -683,6 +686,12 @@ struct K2Impl {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k2_fused_step<L, S, BX, BY, NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k2_fused_step<L, S, BX, BY, NS, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k2_fused_step<L, S, BX, BY, NS, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             sm);
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k2_batched_step<L, S, BX, BY, NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              sm);
     if (e != cudaSuccess) return e;
@@ -694,10 +703,17 @@ struct K2Impl {
     K1Args<float> a = k1_make_args<float>(ctx, ctx->parity, 1 - ctx->parity);
     make_bounce_terms<L, float>(ctx->g, a.bb);
     const int grid = ctx->plan.nbx * ctx->plan.nby * ctx->plan.nbz;
-    if (ctx->g.has_force)
-      k2_fused_step<L, S, BX, BY, NS, true><<<grid, Sh::NT, Sh::SMEM, ctx->stream>>>(ctx->tmap, a);
-    else
-      k2_fused_step<L, S, BX, BY, NS, false><<<grid, Sh::NT, Sh::SMEM, ctx->stream>>>(ctx->tmap, a);
+    cudaStream_t st = ctx->stream;
+    if (ctx->g.zlink[0] || ctx->g.zlink[1]) {
+      if (ctx->g.has_force)
+        k2_fused_step<L, S, BX, BY, NS, true, true><<<grid, Sh::NT, Sh::SMEM, st>>>(ctx->tmap, a);
+      else
+        k2_fused_step<L, S, BX, BY, NS, false, true><<<grid, Sh::NT, Sh::SMEM, st>>>(ctx->tmap, a);
+    } else if (ctx->g.has_force) {
+      k2_fused_step<L, S, BX, BY, NS, true><<<grid, Sh::NT, Sh::SMEM, st>>>(ctx->tmap, a);
+    } else {
+      k2_fused_step<L, S, BX, BY, NS, false><<<grid, Sh::NT, Sh::SMEM, st>>>(ctx->tmap, a);
+    }
     return cudaGetLastError();
   }
 

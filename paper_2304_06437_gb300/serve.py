@@ -107,6 +107,8 @@ class Server:
         self.updates = 0                    # node updates executed
         self.rounds = 0
         self.max_active = 0
+        # host wall time per phase of the rounds (seconds)
+        self.phase_s = {"admit": 0.0, "rebuild": 0.0, "step": 0.0, "retire": 0.0}
 
     # ---------------------------------------------------------------- engine
     def submit(self, req: Request):
@@ -176,20 +178,31 @@ class Server:
     def step_round(self):
         """One round: admit, advance every active domain by round_steps,
         retire converged ones."""
+        t0 = time.perf_counter()
         changed = self._admit()
+        t1 = time.perf_counter()
         if changed or (self.batch is None and self.active):
             self._rebuild()
+        t2 = time.perf_counter()
+        self.phase_s["admit"] += t1 - t0
+        self.phase_s["rebuild"] += t2 - t1
         self.max_active = max(self.max_active, len(self.active))
         if not self.active:
             return
         self.batch.step(self.round_steps)
         self.batch.sync()
+        t3 = time.perf_counter()
         for req, s in self.active:
             req.steps += self.round_steps
             self.updates += s.n * self.round_steps
         self.rounds += 1
-        if self._retire():
+        retired = self._retire()
+        t4 = time.perf_counter()
+        if retired:
             self._rebuild()
+        self.phase_s["step"] += t3 - t2
+        self.phase_s["retire"] += t4 - t3
+        self.phase_s["rebuild"] += time.perf_counter() - t4
 
     def run(self, until: Optional[float] = None, idle_sleep: float = 1e-3):
         """Serve until the queue and the engine are empty (or the clock passes
@@ -227,6 +240,7 @@ class Server:
             "on_gpu_p50_s": pct(gpu, 50), "on_gpu_p99_s": pct(gpu, 99),
             "aggregate_mlups": self.updates / wall_s / 1e6 if wall_s > 0 else None,
             "rounds": self.rounds, "max_active": self.max_active,
+            "host_phase_s": {k: round(v, 3) for k, v in self.phase_s.items()},
         }
 
 
