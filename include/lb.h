@@ -314,6 +314,17 @@ LB_API int lb_batch_create(lb_ctx* const* ctxs, int32_t n, void* stream, lb_batc
  * friends on a member see the batch's steps. */
 LB_API int lb_batch_step(lb_batch* b, int64_t n);
 
+/* lb_reduce for every member in one pass: the FP64 sums of all members are
+ * enqueued on the batch stream (after the batch's steps and the work queued
+ * on the members' own streams) and read back with one copy.  out[6 i + 0] =
+ * mass, [6 i + 1 .. 3] = momentum (user axes), [6 i + 4] = residual (with
+ * want_residual != 0; lb_reduce's definition and history, else 0), [6 i + 5]
+ * = 0 or LB_E_DIVERGED for member i (in the order given to
+ * lb_batch_create).  Synchronises the batch stream.  The first call allocates
+ * the batch's sum buffers (7 doubles per member, device and pinned host).
+ * Errors: LB_E_INVAL, LB_E_NOMEM, LB_E_CUDA. */
+LB_API int lb_batch_reduce(lb_batch* b, int32_t want_residual, double* out);
+
 /* Waits for the batch stream; returns LB_E_TIMEOUT if a kernel of the batch
  * gave up waiting for a copy. */
 LB_API int lb_batch_sync(lb_batch* b);

@@ -147,6 +147,7 @@ SIGNATURES = {
     "lb_batch_step": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "lb_batch_sync": (ctypes.c_int, [_vp]),
     "lb_batch_info": (ctypes.c_int, [_vp, _P(lb_batch_info_t)]),
+    "lb_batch_reduce": (ctypes.c_int, [_vp, ctypes.c_int32, _dp]),
     "lb_batch_destroy": (None, [_vp]),
     "lb_cg_create": (ctypes.c_int, [ctypes.c_int32, _i64p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_int32, _vp, _P(_vp)]),

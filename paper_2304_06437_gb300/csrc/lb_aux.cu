@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(Layout l, const S* __r
     for (int k = 0; k < kRedFields; ++k) partial[k * kRedBlocks + blockIdx.x] = sh[k][0];
 }
 
-__global__ void reduce_final_kernel(double* __restrict__ partial, int nblocks) {
+__global__ void reduce_final_kernel(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
   // one block: fixed-order tree over the block partials
   __shared__ double sh[kThreads];
   for (int k = 0; k < kRedFields; ++k) {
@@ -263,7 +263,7 @@ __global__ void reduce_final_kernel(double* __restrict__ partial, int nblocks) {
       if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
       __syncthreads();
     }
-    if (threadIdx.x == 0) partial[kRedFields * kRedBlocks + k] = sh[0];
+    if (threadIdx.x == 0) out[k] = sh[0];
     __syncthreads();
   }
 }
@@ -384,14 +384,14 @@ cudaError_t aux_get_region(lb_ctx* ctx, const int64_t lo[3], const int64_t size[
   return cudaGetLastError();
 }
 
-cudaError_t aux_reduce(lb_ctx* ctx, double* host_out, bool residual) {
+cudaError_t aux_reduce_enqueue(lb_ctx* ctx, cudaStream_t stream, double* dev_out, bool residual) {
   const Layout l = layout_of(ctx->g);
   const double* F = ctx->g.force;
   cudaError_t err = cudaSuccess;
   if (residual && !ctx->d_uprev) {
-    err = cudaMallocAsync(reinterpret_cast<void**>(&ctx->d_uprev), sizeof(float) * 3 * l.n, ctx->stream);
+    err = cudaMallocAsync(reinterpret_cast<void**>(&ctx->d_uprev), sizeof(float) * 3 * l.n, stream);
     if (err != cudaSuccess) return err;
-    err = cudaMemsetAsync(ctx->d_uprev, 0, sizeof(float) * 3 * l.n, ctx->stream);
+    err = cudaMemsetAsync(ctx->d_uprev, 0, sizeof(float) * 3 * l.n, stream);
     if (err != cudaSuccess) return err;
   }
   dispatch_lattice(ctx->lattice, [&](auto Lt) {
@@ -399,16 +399,20 @@ cudaError_t aux_reduce(lb_ctx* ctx, double* host_out, bool residual) {
     dispatch_storage(ctx->storage, [&](auto St, auto Rt) {
       using S = typename decltype(St)::type;
       using R = typename decltype(Rt)::type;
-      reduce_kernel<L, S, R><<<kRedBlocks, kThreads, 0, ctx->stream>>>(
+      reduce_kernel<L, S, R><<<kRedBlocks, kThreads, 0, stream>>>(
           l, static_cast<const S*>(ctx->f), ctx->g.rho0, F[0], F[1], F[2], ctx->d_uprev, residual ? 1 : 0,
           ctx->d_red);
     });
   });
-  reduce_final_kernel<<<1, kThreads, 0, ctx->stream>>>(ctx->d_red, kRedBlocks);
-  err = cudaGetLastError();
+  reduce_final_kernel<<<1, kThreads, 0, stream>>>(ctx->d_red, kRedBlocks, dev_out);
+  return cudaGetLastError();
+}
+
+cudaError_t aux_reduce(lb_ctx* ctx, double* host_out, bool residual) {
+  double* dev_out = ctx->d_red + kRedFields * kRedBlocks;
+  cudaError_t err = aux_reduce_enqueue(ctx, ctx->stream, dev_out, residual);
   if (err != cudaSuccess) return err;
-  err = cudaMemcpyAsync(host_out, ctx->d_red + kRedFields * kRedBlocks, sizeof(double) * kRedFields,
-                        cudaMemcpyDeviceToHost, ctx->stream);
+  err = cudaMemcpyAsync(host_out, dev_out, sizeof(double) * kRedFields, cudaMemcpyDeviceToHost, ctx->stream);
   if (err != cudaSuccess) return err;
   return cudaStreamSynchronize(ctx->stream);
 }

@@ -48,6 +48,8 @@ struct lb_batch {
   std::vector<cudaEvent_t> ctx_ev;
   int64_t steps_done = 0;
   int64_t total_nodes = 0;
+  double* d_sums = nullptr;  // lb_batch_reduce: seven sums per member (device)
+  double* h_sums = nullptr;  // and their pinned host copy
 };
 
 namespace lbgb {
@@ -392,6 +394,42 @@ int lb_batch_sync(lb_batch* b) {
   return st != 0 ? st : LB_OK;
 }
 
+int lb_batch_reduce(lb_batch* b, int32_t want_residual, double* out) {
+  if (!b || !out) return LB_E_INVAL;
+  DevGuard guard(b->device);
+  const size_t n = b->ctxs.size();
+  if (!b->d_sums) {
+    LB_BTRY(cudaMalloc(reinterpret_cast<void**>(&b->d_sums), n * kReduceFields * sizeof(double)));
+    LB_BTRY(cudaMallocHost(reinterpret_cast<void**>(&b->h_sums), n * kReduceFields * sizeof(double)));
+  }
+  // after the work queued on the members' own streams and the batch's steps
+  for (size_t i = 0; i < n; ++i) {
+    LB_BTRY(cudaEventRecord(b->ctx_ev[i], b->ctxs[i]->stream));
+    LB_BTRY(cudaStreamWaitEvent(b->stream, b->ctx_ev[i], 0));
+  }
+  for (size_t i = 0; i < n; ++i)
+    LB_BTRY(aux_reduce_enqueue(b->ctxs[i], b->stream, b->d_sums + i * kReduceFields, want_residual != 0));
+  LB_BTRY(cudaMemcpyAsync(b->h_sums, b->d_sums, n * kReduceFields * sizeof(double), cudaMemcpyDeviceToHost,
+                          b->stream));
+  // the members' reduction buffers and residual snapshots were used on the
+  // batch stream: later work on a member's stream comes after
+  LB_BTRY(cudaEventRecord(b->done, b->stream));
+  for (lb_ctx* x : b->ctxs) LB_BTRY(cudaStreamWaitEvent(x->stream, b->done, 0));
+  LB_BTRY(cudaStreamSynchronize(b->stream));
+  for (size_t i = 0; i < n; ++i) {
+    double* o = out + 6 * i;
+    double mom[3] = {0, 0, 0}, res = 0.0;
+    const int rc = reduce_finish(b->ctxs[i], b->h_sums + i * kReduceFields, want_residual != 0, &o[0], mom,
+                                 want_residual ? &res : nullptr);
+    o[1] = mom[0];
+    o[2] = mom[1];
+    o[3] = mom[2];
+    o[4] = res;
+    o[5] = rc == LB_OK ? 0.0 : double(rc);
+  }
+  return LB_OK;
+}
+
 int lb_batch_info(const lb_batch* b, lb_batch_info_t* info) {
   if (!b || !info) return LB_E_INVAL;
   std::memset(info, 0, sizeof(*info));
@@ -422,6 +460,8 @@ void lb_batch_destroy(lb_batch* b) {
     if (st) cudaStreamDestroy(st);
   for (cudaEvent_t e : b->ctx_ev)
     if (e) cudaEventDestroy(e);
+  if (b->d_sums) cudaFree(b->d_sums);
+  if (b->h_sums) cudaFreeHost(b->h_sums);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }

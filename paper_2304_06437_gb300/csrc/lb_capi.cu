@@ -667,6 +667,13 @@ int lb_reduce(lb_ctx* ctx, double* mass, double mom[3], double* residual) {
   const bool want_res = residual != nullptr;
   int rc = cuda_status(aux_reduce(ctx, out, want_res));
   if (rc != LB_OK) return rc;
+  return reduce_finish(ctx, out, want_res, mass, mom, residual);
+}
+
+}  // extern "C"
+
+int lbgb::reduce_finish(lb_ctx* ctx, const double* out, bool want_res, double* mass, double mom[3],
+                        double* residual) {
   const int d = ctx->g.d;
   if (mass) *mass = out[0];
   if (mom) {
@@ -683,6 +690,8 @@ int lb_reduce(lb_ctx* ctx, double* mass, double mom[3], double* residual) {
   if (out[6] != 0.0 || !std::isfinite(out[0])) return LB_E_DIVERGED;
   return LB_OK;
 }
+
+extern "C" {
 
 int lb_sync(lb_ctx* ctx) {
   if (!ctx) return LB_E_INVAL;

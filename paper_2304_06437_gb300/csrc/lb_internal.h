@@ -111,6 +111,14 @@ cudaError_t aux_moments_range(lb_ctx* ctx, double* rho, double* u, int64_t n0, i
 cudaError_t aux_get_region(lb_ctx* ctx, const int64_t lo[3], const int64_t size[3], double* f_dev);
 cudaError_t aux_reduce(lb_ctx* ctx, double* host_out /* mass, mom[3], du2, u2, nonfinite */,
                        bool residual);
+// the same sums enqueued on `stream`, the seven values written to dev_out
+// (device memory); nothing is copied to the host or synchronised
+cudaError_t aux_reduce_enqueue(lb_ctx* ctx, cudaStream_t stream, double* dev_out, bool residual);
+constexpr int kReduceFields = 7;
+// lb_reduce's outputs from the seven sums of aux_reduce (lb_capi.cu); returns
+// LB_E_DIVERGED if a value is not finite
+int reduce_finish(lb_ctx* ctx, const double* sums, bool want_residual, double* mass, double mom[3],
+                  double* residual);
 
 // map a user-facing (canonical) vector to internal axes and back
 void to_internal(int d, const double in[3], double out[3]);

@@ -7,10 +7,11 @@ advances all of them together, ``round_steps`` time steps per round, through
 one :class:`~paper_2304_06437_gb300.solver.Batch` (one persistent launch per
 brick-shape class and step, CUDA-graph replays).  Between rounds it
 
-* reads each active domain's FP64 relative velocity residual
-  ||u_t - u_{t-K}|| / ||u_t|| (``lb_reduce``; K = round_steps) and retires the
-  domains that converged or hit their step cap (their rho and u are copied to
-  the host and their device memory freed);
+* reads every active domain's FP64 relative velocity residual
+  ||u_t - u_{t-K}|| / ||u_t|| (K = round_steps) in one batched reduction
+  (``lb_batch_reduce``: one pass per domain on the device, one copy to the
+  host) and retires the domains that converged or hit their step cap (their
+  rho and u are copied to the host and their device memory freed);
 * admits arrived requests (first come first served, or smallest first) while
   the device's free memory minus a reserve covers the request's estimated
   footprint and an optional cap on resident nodes allows, so requests that
@@ -152,8 +153,10 @@ class Server:
 
     def _retire(self) -> bool:
         keep, changed = [], False
-        for req, s in self.active:
-            r = s.reduce(residual=True)["residual"]
+        # the batch's members are the active domains, in this order
+        sums = self.batch.reduce(residual=True)
+        for (req, s), red in zip(self.active, sums):
+            r = red["residual"]
             req.residual = r
             if not math.isfinite(r) or r < req.tol or req.steps >= req.max_steps:
                 req.converged = math.isfinite(r) and r < req.tol

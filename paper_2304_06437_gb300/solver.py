@@ -243,6 +243,23 @@ class Batch:
     def sync(self):
         B.check(self._lib.lb_batch_sync(self._b), "lb_batch_sync")
 
+    def reduce(self, residual=False):
+        """lb_reduce of every member in one pass (lb_batch_reduce): a list of
+        dicts in member order, with "diverged" set where a value is not
+        finite."""
+        n = len(self.solvers)
+        out = np.zeros(6 * n)
+        B.check(self._lib.lb_batch_reduce(self._b, 1 if residual else 0,
+                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "lb_batch_reduce")
+        res = []
+        for i, s in enumerate(self.solvers):
+            o = out[6 * i:6 * i + 6]
+            r = {"mass": float(o[0]), "momentum": [float(v) for v in o[1:4]][: s.d], "diverged": o[5] != 0}
+            if residual:
+                r["residual"] = float(o[4])
+            res.append(r)
+        return res
+
     def info(self) -> dict:
         inf = B.lb_batch_info_t()
         B.check(self._lib.lb_batch_info(self._b, ctypes.byref(inf)), "lb_batch_info")

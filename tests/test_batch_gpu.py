@@ -155,3 +155,30 @@ def test_batch_members_match_oracle(lb):
             assert rel_l2(r, r_ref) < tol and rel_l2(u, u_ref) < tol, (sp, rel_l2(r, r_ref), rel_l2(u, u_ref))
     for s in members:
         s.close()
+
+
+def test_batched_reduction_equals_member_reductions(lb):
+    """lb_batch_reduce: the same FP64 sums, residual history included, as
+    lb_reduce on each member alone (bit for bit), over two rounds."""
+    specs = _specs(13)
+    a = [_make(lb, sp, 700 + i) for i, sp in enumerate(specs)]
+    b = [_make(lb, sp, 700 + i) for i, sp in enumerate(specs)]
+    with lb.Batch(a) as ba, lb.Batch(b) as bb:
+        for rnd in range(2):
+            ba.step(5)
+            bb.step(5)
+            got = ba.reduce(residual=True)
+            bb.sync()
+            want = [s.reduce(residual=True) for s in b]
+            for g, w in zip(got, want):
+                assert g["mass"] == w["mass"] and g["momentum"] == w["momentum"]
+                assert g["residual"] == w["residual"] and not g["diverged"]
+                if rnd == 0:
+                    assert g["residual"] == 1.0
+                else:
+                    assert 0.0 < g["residual"] < 1.0
+        # without the residual: the history is left alone
+        plain = ba.reduce()
+        assert all("residual" not in r for r in plain)
+    for s in a + b:
+        s.close()

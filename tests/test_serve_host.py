@@ -44,6 +44,9 @@ class FakeBatch:
         for s in self.solvers:
             s.step(n)
 
+    def reduce(self, residual=False):
+        return [s.reduce(residual) for s in self.solvers]
+
     def sync(self):
         pass
 
