@@ -413,9 +413,9 @@ LB_API int lb_selftest_timeout(int64_t limit_ns, int64_t* waited_ns);
  * another's memory.  Every slab computes the same bits as the single domain
  * (the shell records are the neighbour's rounded state collided once more).
  *
- * lb_halo_bytes: size of one message of ctx (equal on both sides of a
- *   boundary when the slabs share lattice, storage, the extents of the two
- *   other axes and the brick cross-section).
+ * lb_halo_bytes: size of one message of ctx, a multiple of 16 (equal on both
+ *   sides of a boundary when the slabs share lattice, storage, the extents of
+ *   the two other axes and the brick cross-section).
  * lb_halo_pack: enqueues on the context stream the copy of the records that
  *   leave through face `side` of the current state into buf (device memory
  *   of the context's device, lb_halo_bytes, 16-byte aligned), preceded by a

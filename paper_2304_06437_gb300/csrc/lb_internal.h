@@ -40,6 +40,7 @@ struct FusedPlan {
   int xwarps;              // dedicated export warps (0: node-owning warps export)
   int npt;                 // nodes per thread (1 scalar, 2 paired FP32x2 kernel)
   int ts;                  // 1: completed planes leave through a TMA store
+  int minb;                // CTAs per SM the compiled shape is built for
   size_t smem_bytes;
 };
 

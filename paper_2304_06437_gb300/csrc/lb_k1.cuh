@@ -106,7 +106,9 @@ __device__ __forceinline__ int lat_slot_of_sub(int ia) {
   return r;
 }
 
-template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, int TS = 0>
+// MINB: CTAs the shape is compiled to keep resident on one SM (registers
+// capped at 64K / (MINB x threads), shared memory within 228 KB / MINB)
+template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, int TS = 0, int MINB = 1>
 struct K1Shape {
   static constexpr int Q = L::Q;
   static constexpr int NTM = BX * BY;        // threads that own a node
@@ -157,7 +159,8 @@ struct K1Shape {
   // per plane) instead of in registers -- for up to 19 velocities (measured:
   // FP16 D3Q19 2 % faster, D3Q27 with three entries per thread 1 % slower)
   static constexpr size_t HDESC = size_t(HPT) * NT * 16;
-  static constexpr bool HSMEM = SMEM0 + HDESC <= size_t(227) * 1024 && Q <= 19;
+  static constexpr size_t SMEM_CAP = (size_t(228) * 1024) / MINB - 1024;
+  static constexpr bool HSMEM = SMEM0 + HDESC <= SMEM_CAP && Q <= 19;
   static constexpr size_t OFF_HDESC = SMEM0;
   static constexpr size_t SMEM = SMEM0 + (HSMEM ? HDESC : 0);
   // the plane sweep runs three planes per loop trip (the three gathered
@@ -166,8 +169,9 @@ struct K1Shape {
   // FP32 arithmetic values per node, or 27 in a CTA of at most 256 threads,
   // and not with BF16 storage, whose rounding takes the registers that the
   // unrolled body would need
-  static constexpr bool UNROLL3 = (Q * sizeof(R) <= 76 || (Q * sizeof(R) <= 108 && NT <= 256)) &&
+  static constexpr bool UNROLL3 = (Q * sizeof(R) <= 76 || (Q * sizeof(R) <= 108 && NT * MINB <= 256)) &&
                                   !std::is_same<S, __nv_bfloat16>::value;
+  static_assert(SMEM <= SMEM_CAP, "shared memory of the shape exceeds its share of the SM");
   static_assert(BY == 1 || NYF > 0, "a 2D brick has one internal row");
   static_assert(NXW > 0 || 32 * NEXW <= NTM, "export entries need more warps than the CTA has");
   static_assert(WB == 1 || WB == 2, "one or two window buffers");
@@ -330,10 +334,10 @@ __device__ __forceinline__ void export_one_face(const K1Args<R>& args, const R (
 // LINK: compiled for contexts with a link face (slab decomposition); the
 // other instantiations compile the plain form, whose shell has no ghosts.
 template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE, int TS = 0,
-          bool LINK = false>
+          bool LINK = false, int MINB = 1>
 __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args<R>& args, const int bI,
                                          const int bJ, const int bK) {
-  using Sh = K1Shape<L, S, R, BX, BY, NS, WB, NXW, TS>;
+  using Sh = K1Shape<L, S, R, BX, BY, NS, WB, NXW, TS, MINB>;
   static_assert(WB == 2, "the pipelined sweep needs two window buffers");
   constexpr int Q = L::Q;
   constexpr int NTM = Sh::NTM;
@@ -904,13 +908,13 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
 
 // One launch per time step of one domain: one CTA per brick column.
 template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE, int TS = 0,
-          bool LINK = false>
-__global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
+          bool LINK = false, int MINB = 1>
+__global__ void __launch_bounds__(BX* BY + 32 * NXW, MINB)
     k1_fused_step(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ K1Args<R> args) {
   const int nbx = args.nbx, nby = args.nby;
   const int b = blockIdx.x;
-  k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE, TS, LINK>(&tmap, args, b % nbx, (b / nbx) % nby,
-                                                          b / (nbx * nby));
+  k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE, TS, LINK, MINB>(&tmap, args, b % nbx, (b / nbx) % nby,
+                                                                b / (nbx * nby));
 }
 
 // One launch per time step of many domains (a batch): a persistent grid whose
@@ -918,8 +922,9 @@ __global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
 // (domain, bI, bJ, bK); the arguments of domain d at shell parity p are
 // args[p * n_dom + d], and domain d's parity at this launch is
 // (dom_par[d] + k) & 1.
-template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE, int TS = 0>
-__global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
+template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE, int TS = 0,
+          int MINB = 1>
+__global__ void __launch_bounds__(BX* BY + 32 * NXW, MINB)
     k1_batched_step(const K1Args<R>* __restrict__ args, int n_dom, const CUtensorMap* __restrict__ tmaps,
                     const int4* __restrict__ items, const int* __restrict__ starts, const int* __restrict__ dom_par,
                     int k) {
@@ -927,7 +932,7 @@ __global__ void __launch_bounds__(BX* BY + 32 * NXW, 1)
   for (int i = starts[blockIdx.x]; i < i1; ++i) {
     const int4 it = items[i];
     const int p = (dom_par[it.x] + k) & 1;
-    if (!k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE, TS>(tmaps + it.x, args[size_t(p) * n_dom + it.x], it.y,
+    if (!k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE, TS, false, MINB>(tmaps + it.x, args[size_t(p) * n_dom + it.x], it.y,
                                                            it.z, it.w))
       return;
   }

@@ -33,6 +33,7 @@ struct K1Variant {
   cudaError_t (*batched)(const BatchLaunch&, cudaStream_t);
   int (*batched_occupancy)();
   int ts;  // 1: completed planes leave through a TMA store (scalar kernel only)
+  int minb;  // CTAs per SM the shape is compiled for
 };
 
 // the compiled shape a fused-scheme context runs (lb_k1_plan.cu)
@@ -76,22 +77,22 @@ K1Args<R> k1_make_args(lb_ctx* ctx, int cur_parity, int next_parity) {
   return a;
 }
 
-template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, int TS = 0>
+template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, int TS = 0, int MINB = 1>
 struct K1Impl {
-  using Sh = K1Shape<L, S, R, BX, BY, NS, WB, NXW, TS>;
+  using Sh = K1Shape<L, S, R, BX, BY, NS, WB, NXW, TS, MINB>;
 
   static cudaError_t configure() {
     const int sm = int(Sh::SMEM);
-    cudaError_t e = cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false, TS>,
+    cudaError_t e = cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false, TS, false, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true, TS>,
+      e = cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true, TS, false, MINB>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false, TS, true>,
+      e = cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false, TS, true, MINB>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true, TS, true>,
+      e = cudaFuncSetAttribute(k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true, TS, true, MINB>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     return e;
   }
@@ -104,13 +105,13 @@ struct K1Impl {
     cudaStream_t st = ctx->stream;
     if (link) {
       if (ctx->g.has_force)
-        k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true, TS, true><<<grid, Sh::NT, Sh::SMEM, st>>>(ctx->tmap, a);
+        k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true, TS, true, MINB><<<grid, Sh::NT, Sh::SMEM, st>>>(ctx->tmap, a);
       else
-        k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false, TS, true><<<grid, Sh::NT, Sh::SMEM, st>>>(ctx->tmap, a);
+        k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false, TS, true, MINB><<<grid, Sh::NT, Sh::SMEM, st>>>(ctx->tmap, a);
     } else if (ctx->g.has_force) {
-      k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true, TS><<<grid, Sh::NT, Sh::SMEM, st>>>(ctx->tmap, a);
+      k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, true, TS, false, MINB><<<grid, Sh::NT, Sh::SMEM, st>>>(ctx->tmap, a);
     } else {
-      k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false, TS><<<grid, Sh::NT, Sh::SMEM, st>>>(ctx->tmap, a);
+      k1_fused_step<L, S, R, BX, BY, NS, WB, NXW, false, TS, false, MINB><<<grid, Sh::NT, Sh::SMEM, st>>>(ctx->tmap, a);
     }
     return cudaGetLastError();
   }
@@ -131,10 +132,10 @@ struct K1Impl {
   static cudaError_t batched(const BatchLaunch& b, cudaStream_t stream) {
     const K1Args<R>* args = static_cast<const K1Args<R>*>(b.args);
     if (b.force)
-      k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true, TS><<<b.grid, Sh::NT, Sh::SMEM, stream>>>(
+      k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true, TS, MINB><<<b.grid, Sh::NT, Sh::SMEM, stream>>>(
           args, b.n_dom, b.tmaps, b.items, b.starts, b.dom_par, b.k);
     else
-      k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, false, TS><<<b.grid, Sh::NT, Sh::SMEM, stream>>>(
+      k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, false, TS, MINB><<<b.grid, Sh::NT, Sh::SMEM, stream>>>(
           args, b.n_dom, b.tmaps, b.items, b.starts, b.dom_par, b.k);
     return cudaGetLastError();
   }
@@ -142,13 +143,13 @@ struct K1Impl {
   static int batched_occupancy() {
     const int sm = int(Sh::SMEM);
     if (configure() != cudaSuccess) return 0;
-    if (cudaFuncSetAttribute(k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, false, TS>,
+    if (cudaFuncSetAttribute(k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, false, TS, MINB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
-        cudaFuncSetAttribute(k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true, TS>,
+        cudaFuncSetAttribute(k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true, TS, MINB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
       return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true, TS>, Sh::NT,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true, TS, MINB>, Sh::NT,
                                                       Sh::SMEM) != cudaSuccess)
       return 0;
     return n;
@@ -156,7 +157,7 @@ struct K1Impl {
 
   static constexpr K1Variant variant(int lattice, int storage) {
     return K1Variant{lattice, storage, BX, BY, NS, WB, NXW, Sh::SMEM, &configure, &step, &bootstrap, 1, &batched,
-                     &batched_occupancy, TS};
+                     &batched_occupancy, TS, MINB};
   }
 };
 

@@ -43,9 +43,9 @@ static int variant_lists(int lattice, const K1Variant* lists[2], int counts[2]) 
 }
 
 // The first compiled shape that matches (lattice, storage, bx, by, ns, wb,
-// nxw, npt, ts); zero fields (negative nxw, ts) match anything.
+// nxw, npt, ts, minb); zero fields (negative nxw, ts) match anything.
 static const K1Variant* find_variant(int lattice, int storage, int bx, int by, int ns, int wb, int nxw, int npt,
-                                     int ts) {
+                                     int ts, int minb = 0) {
   const K1Variant* lists[2];
   int counts[2];
   const int nl = variant_lists(lattice, lists, counts);
@@ -60,24 +60,27 @@ static const K1Variant* find_variant(int lattice, int storage, int bx, int by, i
       if (nxw >= 0 && v.nxw != nxw) continue;
       if (npt > 0 && v.npt != npt) continue;
       if (ts >= 0 && v.ts != ts) continue;
+      if (minb > 0 && v.minb != minb) continue;
       return &v;
     }
   }
   return nullptr;
 }
 
-// Optional pipeline request from the environment, "NS,WB[,NXW[,NPT[,TS]]]"
-// (TMA slots, window buffers, dedicated export warps, nodes per thread, TMA
-// store of completed planes), used to compare the compiled alternatives of a
-// brick shape; 0 (-1 for NXW and TS) = any.
-static void pipeline_request(int* ns, int* wb, int* nxw, int* npt, int* ts) {
+// Optional pipeline request from the environment,
+// "NS,WB[,NXW[,NPT[,TS[,MINB]]]]" (TMA slots, window buffers, dedicated
+// export warps, nodes per thread, TMA store of completed planes, CTAs per
+// SM), used to compare the compiled alternatives of a brick shape; 0 (-1 for
+// NXW and TS) = any.
+static void pipeline_request(int* ns, int* wb, int* nxw, int* npt, int* ts, int* minb) {
   *ns = 0;
   *wb = 0;
   *nxw = -1;
   *npt = 0;
   *ts = -1;
+  *minb = 0;
   const char* e = std::getenv("LB_FUSED_PIPELINE");
-  if (e) std::sscanf(e, "%d,%d,%d,%d,%d", ns, wb, nxw, npt, ts);
+  if (e) std::sscanf(e, "%d,%d,%d,%d,%d,%d", ns, wb, nxw, npt, ts, minb);
 }
 
 static int sm_count() {
@@ -119,11 +122,14 @@ static void fill_plan(const Geometry& g, const K1Variant* v, int req_bz, FusedPl
   p.xwarps = v->nxw;
   p.npt = v->npt;
   p.ts = v->ts;
+  p.minb = v->minb;
   p.smem_bytes = v->smem;
   p.nbx = (g.nx + p.bx - 1) / p.bx;
   p.nby = (g.ny + p.by - 1) / p.by;
   const int columns = p.nbx * p.nby;
-  p.bz = req_bz > 0 ? (req_bz < g.nz ? req_bz : g.nz) : choose_bz(g.nz, columns, p.slots, sms > 0 ? sms : sm_count());
+  // resident CTAs: the SMs times the CTAs one SM holds of this shape
+  const int slots_gpu = (sms > 0 ? sms : sm_count()) * (v->minb > 0 ? v->minb : 1);
+  p.bz = req_bz > 0 ? (req_bz < g.nz ? req_bz : g.nz) : choose_bz(g.nz, columns, p.slots, slots_gpu);
   p.nbz = (g.nz + p.bz - 1) / p.bz;
   int nxf = 0, nyf = 0, nzf = 0;
   dispatch_lattice(g.lattice, [&](auto Lt) {
@@ -148,9 +154,9 @@ static void fill_plan(const Geometry& g, const K1Variant* v, int req_bz, FusedPl
 bool k1_plan(const Geometry& g, int storage, const int32_t tile_req[3], FusedPlan* plan, int sms) {
   const int rbx = tile_req ? tile_req[0] : 0;
   const int rby = tile_req ? tile_req[1] : 0;
-  int rns, rwb, rnxw, rnpt, rts;
-  pipeline_request(&rns, &rwb, &rnxw, &rnpt, &rts);
-  const K1Variant* v = find_variant(g.lattice, storage, rbx, rby, rns, rwb, rnxw, rnpt, rts);
+  int rns, rwb, rnxw, rnpt, rts, rminb;
+  pipeline_request(&rns, &rwb, &rnxw, &rnpt, &rts, &rminb);
+  const K1Variant* v = find_variant(g.lattice, storage, rbx, rby, rns, rwb, rnxw, rnpt, rts, rminb);
   if (!v) return false;
   fill_plan(g, v, tile_req ? tile_req[2] : 0, plan, sms);
   return true;
@@ -179,7 +185,7 @@ int k1_variants_for(int lattice, int storage, const void** out, int cap) {
 
 static const K1Variant* ctx_variant(lb_ctx* ctx) {
   return find_variant(ctx->lattice, ctx->storage, ctx->plan.bx, ctx->plan.by, ctx->plan.slots, ctx->plan.wbuf,
-                      ctx->plan.xwarps, ctx->plan.npt, ctx->plan.ts);
+                      ctx->plan.xwarps, ctx->plan.npt, ctx->plan.ts, ctx->plan.minb);
 }
 
 const K1Variant* k1_ctx_variant(lb_ctx* ctx) { return ctx_variant(ctx); }

@@ -740,7 +740,7 @@ struct K2Impl {
   static constexpr K1Variant variant(int lattice, int storage) {
     // the shell format is the scalar kernel's, so its bootstrap is reused
     return K1Variant{lattice, storage, BX, BY, NS, 2, 0, Sh::SMEM, &configure, &step,
-                     &K1Impl<L, S, float, BX, BY, NS, 2, 0>::bootstrap, 2, &batched, &batched_occupancy, 0};
+                     &K1Impl<L, S, float, BX, BY, NS, 2, 0>::bootstrap, 2, &batched, &batched_occupancy, 0, 1};
   }
 };
 

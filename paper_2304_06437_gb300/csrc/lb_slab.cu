@@ -96,9 +96,11 @@ HaloMap halo_map(const lb_ctx* ctx, int side, bool outgoing) {
   return m;
 }
 
+// header + body, rounded up to 16 bytes so that messages laid out back to
+// back in one buffer stay aligned
 int64_t message_bytes(const lb_ctx* ctx) {
   const HaloMap m = halo_map(ctx, 0, true);
-  return int64_t(kHeaderWords) * 8 + m.total * int64_t(ctx->real_bytes);
+  return (int64_t(kHeaderWords) * 8 + m.total * int64_t(ctx->real_bytes) + 15) / 16 * 16;
 }
 
 // Grid-stride copy of the three regions; blockIdx.y selects the region.  On

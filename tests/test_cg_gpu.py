@@ -56,7 +56,7 @@ def test_cg_matches_oracle(lb, lat, dims, storage, ftol, tol):
     fr20, fb20 = oracle.cg_run(cfg, fr0, fb0, 20)
     R0, B0, u0 = oracle.cg_fields(cfg, fr20, fb20)
     assert rel_l2(R, R0) < tol and rel_l2(Bc, B0) < tol
-    assert rel_l2(uu, u0) < tol * 10, rel_l2(uu, u0)
+    assert rel_l2(uu, u0) < tol, rel_l2(uu, u0)
 
 
 def test_cg_init_matches_oracle_init(lb):
@@ -158,7 +158,7 @@ def test_cg_nci_matches_oracle(lb, lat, storage, ftol, tol):
         R, Bc, uu = s.fields()
     R20, B20, u20 = oracle.cg_fields(cfg, *oracle.cg_run(cfg, fr0, fb0, 20))
     assert rel_l2(R, R20) < tol and rel_l2(Bc, B20) < tol
-    assert rel_l2(uu, u20) < tol * 10, rel_l2(uu, u20)
+    assert rel_l2(uu, u20) < tol, rel_l2(uu, u20)
 
 
 def test_cg_nci_off_equals_plain_and_arguments_checked(lb):

@@ -35,10 +35,12 @@ def _dims(lat):
     return (300, 23, 1) if dim_of(lat) == 2 else (37, 21, 23)
 
 
-def _single(lb, lat, dims, faces, wall_u, storage, force, f0, steps, tile):
+def _single(lb, lat, dims, faces, wall_u, storage, force, f0, steps, tile, moments=False):
     with lb.Solver(lat, dims, 0.61, faces=faces, wall_u=wall_u, storage=storage, force=force, tile=tile) as s:
         s.set_populations(np.ascontiguousarray(f0))
         s.step(steps)
+        if moments:
+            return (s.get_populations(),) + s.moments()
         return s.get_populations()
 
 
@@ -81,7 +83,7 @@ def test_slab_groups_equal_the_single_domain_bitwise(lb, lat, fname, storage, nr
         import oracle
         f0 = round_populations(f0, oracle.lattice_tables(lat)[1], storage)
     steps = 6
-    ref = _single(lb, lat, dims, faces, wall_u, storage, (0, 0, 0), f0, steps, None)
+    ref, r_ref, u_ref = _single(lb, lat, dims, faces, wall_u, storage, (0, 0, 0), f0, steps, None, moments=True)
     with lb.SlabGroup(lat, dims, 0.61, nranks=nranks, counts=counts, faces=faces, wall_u=wall_u,
                       storage=storage) as g:
         g.set_populations(f0)
@@ -91,9 +93,6 @@ def test_slab_groups_equal_the_single_domain_bitwise(lb, lat, fname, storage, nr
         got = g.get_populations()
         rho, u = g.moments()
     assert np.array_equal(got, ref)
-    with lb.Solver(lat, dims, 0.61, faces=faces, wall_u=wall_u, storage=storage) as s:
-        s.set_populations(np.ascontiguousarray(ref))
-        r_ref, u_ref = s.moments()
     assert np.array_equal(rho, r_ref) and np.array_equal(u, u_ref)
 
 
@@ -119,7 +118,7 @@ def test_halo_calls_by_hand_and_a_mismatched_message(lb):
         s.set_populations(np.ascontiguousarray(f0[:, n0:n0 + nz[r] * plane]))
         parts.append(s)
     nbytes = parts[0].halo_bytes()
-    assert nbytes == parts[1].halo_bytes() and nbytes % 16 == 0
+    assert nbytes == parts[1].halo_bytes() and nbytes % 16 == 0  # back-to-back messages stay aligned
     msg = [torch.empty(nbytes, dtype=torch.uint8, device="cuda") for _ in range(2)]
     for _ in range(5):
         parts[0].halo_pack(1, msg[0])
@@ -138,12 +137,13 @@ def test_halo_calls_by_hand_and_a_mismatched_message(lb):
     # a face that is not a link has no halo
     with pytest.raises(lb.LBError):
         parts[0].halo_pack(0, msg[0])
-    # a message packed for the same face is refused by the unpack kernel,
-    # which records LB_E_INVAL for the next sync and copies nothing
-    parts[1].halo_pack(0, msg[1])
-    parts[1].sync()
+    # a message packed for the same face (rank 0's own high face, not a low
+    # face) is refused by the unpack kernel, which records LB_E_INVAL for the
+    # next sync and copies nothing
+    parts[0].halo_pack(1, msg[0])
+    parts[0].sync()
     before = parts[0].get_populations()
-    parts[0].halo_unpack(1, msg[1])
+    parts[0].halo_unpack(1, msg[0])
     with pytest.raises(lb.LBError) as e:
         parts[0].sync()
     assert e.value.code == B.LB_E_INVAL
