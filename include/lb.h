@@ -64,6 +64,7 @@ extern "C" {
 #define LB_E_TIMEOUT (-5)     /* a kernel gave up waiting for an asynchronous copy */
 #define LB_E_UNSUPPORTED (-6) /* valid request this build does not implement */
 #define LB_E_TOO_LARGE (-7)   /* grid exceeds the fixed scratch of lb_step_noalloc */
+#define LB_E_ABANDONED (-8)   /* a kernel timed out and could not confirm that its copies ended */
 
 typedef enum { LB_D2Q9 = 0, LB_D3Q19 = 1, LB_D3Q27 = 2 } lb_lattice;
 /* LB_LINK: the face borders the slab of another context (a rank boundary of
@@ -169,7 +170,14 @@ LB_API int lb_moments(lb_ctx* ctx, double* rho, double* u, int32_t on_device);
  * LB_E_DIVERGED if a value is not finite. */
 LB_API int lb_reduce(lb_ctx* ctx, double* mass, double mom[3], double* residual);
 
-/* Waits for the context stream; reports a sticky kernel status (LB_E_TIMEOUT). */
+/* Waits for the context stream; reports the context's sticky kernel status:
+ * LB_E_TIMEOUT (a kernel gave up waiting for one of its copies: the
+ * populations and the shell are undefined), LB_E_ABANDONED (the same, and
+ * the kernel's bounded wait for its own copies still in flight ran out too:
+ * destroy the context, its device memory may still be written), LB_E_INVAL
+ * (lb_halo_unpack refused a message).  Setting the state from outside
+ * (lb_init_moments, lb_init_uniform, lb_set_populations) clears LB_E_TIMEOUT
+ * and LB_E_INVAL; LB_E_ABANDONED stays. */
 LB_API int lb_sync(lb_ctx* ctx);
 
 /* Frees everything the context owns.  NULL is allowed. */

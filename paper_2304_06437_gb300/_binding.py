@@ -20,6 +20,7 @@ LB_E_DIVERGED = -4
 LB_E_TIMEOUT = -5
 LB_E_UNSUPPORTED = -6
 LB_E_TOO_LARGE = -7
+LB_E_ABANDONED = -8
 LB_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 LB_D2Q9, LB_D3Q19, LB_D3Q27 = 0, 1, 2

@@ -134,9 +134,19 @@ void unstage(lb_ctx* ctx, Staged* s) {
   s->owned = false;
 }
 
+// a state set from outside makes the context usable again after a timeout or
+// a refused halo message; an abandoned kernel's status stays
+__global__ void clear_status_kernel(int* status) {
+  if (*status != LB_E_ABANDONED) *status = 0;
+}
+
 int after_state_change(lb_ctx* ctx) {
   if (ctx->scheme == LB_SCHEME_FUSED) LB_TRY_CUDA(k1_bootstrap(ctx));
   if (ctx->d_uprev) ctx->have_uprev = false;
+  if (ctx->d_status) {
+    clear_status_kernel<<<1, 1, 0, ctx->stream>>>(ctx->d_status);
+    LB_TRY_CUDA(cudaGetLastError());
+  }
   return LB_OK;
 }
 
@@ -215,6 +225,7 @@ const char* lb_status_string(int code) {
     case LB_E_TIMEOUT: return "kernel wait timed out";
     case LB_E_UNSUPPORTED: return "unsupported by this build";
     case LB_E_TOO_LARGE: return "grid exceeds the no-allocation scratch size";
+    case LB_E_ABANDONED: return "kernel timed out and its copies were not confirmed finished";
     default: return "unknown status";
   }
 }

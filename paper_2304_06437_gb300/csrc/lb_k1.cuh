@@ -676,8 +676,12 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
     if (tid == 0) {
       if constexpr (TS != 0) bulk_wait_all();
       atomicExch(args.status, LB_E_TIMEOUT);
-      // drain this CTA's own copies still in flight (bounded)
-      for (int kk = (k < 0 ? 0 : k); kk < issued; ++kk) mbar_wait_bounded(&bars[kk % NS], (kk / NS) & 1, kWaitLimitNs);
+      // drain this CTA's own copies still in flight (bounded); a copy that
+      // does not land in time may still write this CTA's shared memory
+      bool drained = true;
+      for (int kk = (k < 0 ? 0 : k); kk < issued; ++kk)
+        drained &= mbar_wait_bounded(&bars[kk % NS], (kk / NS) & 1, kWaitLimitNs);
+      if (!drained) atomicExch(args.status, LB_E_ABANDONED);
     }
   };
 

@@ -422,7 +422,12 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
   auto abort_cta = [&](int k) {
     if (tid == 0) {
       atomicExch(args.status, LB_E_TIMEOUT);
-      for (int kk = (k < 0 ? 0 : k); kk < issued; ++kk) mbar_wait_bounded(&bars[kk % NS], (kk / NS) & 1, kWaitLimitNs);
+      // drain this CTA's own copies still in flight (bounded); a copy that
+      // does not land in time may still write this CTA's shared memory
+      bool drained = true;
+      for (int kk = (k < 0 ? 0 : k); kk < issued; ++kk)
+        drained &= mbar_wait_bounded(&bars[kk % NS], (kk / NS) & 1, kWaitLimitNs);
+      if (!drained) atomicExch(args.status, LB_E_ABANDONED);
     }
   };
 

@@ -148,5 +148,10 @@ def test_halo_calls_by_hand_and_a_mismatched_message(lb):
         parts[0].sync()
     assert e.value.code == B.LB_E_INVAL
     assert np.array_equal(parts[0].get_populations(), before)
+    # the status is sticky until the state is set from outside
+    with pytest.raises(lb.LBError):
+        parts[0].sync()
+    parts[0].set_populations(before)
+    parts[0].sync()
     for s in parts:
         s.close()
