@@ -8,17 +8,19 @@
 namespace lbgb {
 
 extern const K1Variant k1_variants_d3q19[] = {
+    K1Impl<D3Q19, float, float, 32,16,3,2,0>::variant(LB_D3Q19, LB_F32),
     K1Impl<D3Q19, float, float, 64,8,3,2,0>::variant(LB_D3Q19, LB_F32),
     K1Impl<D3Q19, float, float, 64,7,3,2,2>::variant(LB_D3Q19, LB_F32),    // + 2 decoupled export warps
     K1Impl<D3Q19, float, float, 64,6,3,2,4>::variant(LB_D3Q19, LB_F32),    // + 4 decoupled export warps
     K1Impl<D3Q19, float, float, 64,8,2,2,0,1>::variant(LB_D3Q19, LB_F32),  // planes stored by TMA
     K1Impl<D3Q19, float, float, 32,8,2,2,0>::variant(LB_D3Q19, LB_F32),  // small domains (batches)
-    K1Impl<D3Q19, float, float, 32,16,3,2,0>::variant(LB_D3Q19, LB_F32),    // a third less shell traffic
     K1Impl<D3Q19, double, double, 32,8,2,2,0>::variant(LB_D3Q19, LB_F64),
     K1Impl<D3Q19, __half, float, 64,8,4,2,0>::variant(LB_D3Q19, LB_F16S),
     K1Impl<D3Q19, __half, float, 32,8,3,2,0>::variant(LB_D3Q19, LB_F16S),
     K1Impl<D3Q19, __half, float, 64,7,4,2,2>::variant(LB_D3Q19, LB_F16S),
+    K1Impl<D3Q19, __half, float, 32,16,4,2,0>::variant(LB_D3Q19, LB_F16S),
     K1Impl<D3Q19, __nv_bfloat16, float, 64,8,4,2,0>::variant(LB_D3Q19, LB_BF16S),
+    K1Impl<D3Q19, __nv_bfloat16, float, 32,16,4,2,0>::variant(LB_D3Q19, LB_BF16S),
 };
 extern const int k1_n_variants_d3q19 = sizeof(k1_variants_d3q19) / sizeof(k1_variants_d3q19[0]);
 
