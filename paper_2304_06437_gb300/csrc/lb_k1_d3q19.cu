@@ -8,8 +8,8 @@
 namespace lbgb {
 
 extern const K1Variant k1_variants_d3q19[] = {
-    K1Impl<D3Q19, float, float, 32,16,3,2,0>::variant(LB_D3Q19, LB_F32),
     K1Impl<D3Q19, float, float, 64,8,3,2,0>::variant(LB_D3Q19, LB_F32),
+    K1Impl<D3Q19, float, float, 32,16,3,2,0>::variant(LB_D3Q19, LB_F32),   // less shell traffic, equal rate
     K1Impl<D3Q19, float, float, 64,7,3,2,2>::variant(LB_D3Q19, LB_F32),    // + 2 decoupled export warps
     K1Impl<D3Q19, float, float, 64,6,3,2,4>::variant(LB_D3Q19, LB_F32),    // + 4 decoupled export warps
     K1Impl<D3Q19, float, float, 64,8,2,2,0,1>::variant(LB_D3Q19, LB_F32),  // planes stored by TMA

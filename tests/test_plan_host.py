@@ -54,9 +54,9 @@ def _check(lat, dims, p, sms=152):
 
 
 @pytest.mark.parametrize("lat,dims,storage,tile", [
-    ("D3Q19", (1024, 1024, 1024), "f32", (32, 16, 512)),
+    ("D3Q19", (1024, 1024, 1024), "f32", (64, 8, 512)),
     ("D3Q19", (1024, 1024, 1024), "f16s", (64, 8, 512)),
-    ("D3Q27", (512, 512, 512), "f32", (32, 12, 171)),
+    ("D3Q27", (512, 512, 512), "f32", (32, 14, 512)),
     ("D2Q9", (16384, 16384), "f32", (256, 1, 863)),
 ])
 def test_benchmark_configurations_get_their_measured_bricks(P, lat, dims, storage, tile):
