@@ -18,9 +18,7 @@ extern const K1Variant k1_variants_d3q19[] = {
     K1Impl<D3Q19, __half, float, 64,8,4,2,0>::variant(LB_D3Q19, LB_F16S),
     K1Impl<D3Q19, __half, float, 32,8,3,2,0>::variant(LB_D3Q19, LB_F16S),
     K1Impl<D3Q19, __half, float, 64,7,4,2,2>::variant(LB_D3Q19, LB_F16S),
-    K1Impl<D3Q19, __half, float, 32,16,4,2,0>::variant(LB_D3Q19, LB_F16S),
     K1Impl<D3Q19, __nv_bfloat16, float, 64,8,4,2,0>::variant(LB_D3Q19, LB_BF16S),
-    K1Impl<D3Q19, __nv_bfloat16, float, 32,16,4,2,0>::variant(LB_D3Q19, LB_BF16S),
 };
 extern const int k1_n_variants_d3q19 = sizeof(k1_variants_d3q19) / sizeof(k1_variants_d3q19[0]);
 

@@ -9,7 +9,6 @@ namespace lbgb {
 
 extern const K1Variant k1_variants_d3q27[] = {
     K1Impl<D3Q27, float, float, 32,14,2,2,0>::variant(LB_D3Q27, LB_F32),  // 14 warps at 128 registers
-    K1Impl<D3Q27, float, float, 32,16,1,2,0>::variant(LB_D3Q27, LB_F32),  // 16 warps, one TMA slot
     K1Impl<D3Q27, float, float, 32,12,2,2,0>::variant(LB_D3Q27, LB_F32),
     K1Impl<D3Q27, float, float, 32,10,2,2,2>::variant(LB_D3Q27, LB_F32),  // + 2 decoupled export warps
     K1Impl<D3Q27, float, float, 32,10,3,2,0>::variant(LB_D3Q27, LB_F32),  // deeper TMA ring
