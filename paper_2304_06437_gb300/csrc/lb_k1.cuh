@@ -166,11 +166,8 @@ struct K1Shape {
   // the plane sweep runs three planes per loop trip (the three gathered
   // sets change roles at compile time instead of being copied every plane)
   // where the three copies of the body still fit the registers: up to 19
-  // FP32 arithmetic values per node, or 27 in a CTA of at most 256 threads,
-  // and not with BF16 storage, whose rounding takes the registers that the
-  // unrolled body would need
-  static constexpr bool UNROLL3 = (Q * sizeof(R) <= 76 || (Q * sizeof(R) <= 108 && NT * MINB <= 256)) &&
-                                  !std::is_same<S, __nv_bfloat16>::value;
+  // FP32 arithmetic values per node, or 27 in a CTA of at most 256 threads
+  static constexpr bool UNROLL3 = (Q * sizeof(R) <= 76 || (Q * sizeof(R) <= 108 && NT * MINB <= 256));
   static_assert(SMEM <= SMEM_CAP, "shared memory of the shape exceeds its share of the SM");
   static_assert(BY == 1 || NYF > 0, "a 2D brick has one internal row");
   static_assert(NXW > 0 || 32 * NEXW <= NTM, "export entries need more warps than the CTA has");
@@ -573,7 +570,6 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   }
   // (the first barrier of the sweep orders these writes before their use)
 
-  constexpr bool kLateExport = std::is_same<S, __nv_bfloat16>::value;
   auto export_staged = [&](int zx, int sslot) {
     if (exp_warp && zx >= z0 && zx < z1) {
       R* shn = args.sh_next;
@@ -727,10 +723,8 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
       const bool need_g = plane_needed(g);
 
       // exports of plane g - 2 (staged one iteration ago) first: they need
-      // no TMA data, so they overlap the wait for plane c's load (BF16
-      // storage keeps them after the gather: its rounding needs registers
-      // that the earlier placement would spill)
-      if constexpr (!DEC && !kLateExport) export_staged(g - 2, (g - 2) & 1);
+      // no TMA data, so they overlap the wait for plane c's load
+      if constexpr (!DEC) export_staged(g - 2, (g - 2) & 1);
 
       R onl_c[3] = {R(0), R(0), R(0)};
       bool ok = true;
@@ -752,7 +746,6 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
           if constexpr (cz == 1) G2[a] = v;
         });
       }
-      if constexpr (!DEC && kLateExport) export_staged(g - 2, (g - 2) & 1);
 
       // z-descending bounce-backs of plane g - 1, saved one plane ago
       if (bdn_mask) {
