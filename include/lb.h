@@ -301,7 +301,9 @@ LB_API int lb_autotune(lb_ctx* ctx, int32_t steps, lb_tune_entry* table, int32_t
  * batch is destroyed; results are unchanged, every plan gives the same bits):
  * the preferred compiled brick shape that pads the domain's cross-section by
  * at most 25 % (else the least padded one), and one brick per column for
- * sweeps of up to 256 planes.  Classes run on parallel branches of the graph.
+ * sweeps of up to 256 planes; where a class would then have fewer than two
+ * bricks per persistent CTA, its members' sweeps are halved (down to 64
+ * planes) until it has.  Classes run on parallel branches of the graph.
  * stream: cudaStream_t for the batch's work, NULL = a library-owned stream.
  * Errors: LB_E_INVAL (NULL, duplicates, mixed devices), LB_E_UNSUPPORTED,
  * LB_E_NOMEM, LB_E_CUDA. */

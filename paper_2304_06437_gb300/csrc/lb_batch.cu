@@ -86,6 +86,8 @@ void free_class(lb_batch::Class& c) {
 }
 
 // Static balance: bricks by decreasing cost, each to the least-loaded CTA.
+// A brick costs its full cross-section times its planes plus the pipeline
+// fill: the warps of a ragged brick issue for their idle lanes too.
 void build_work_list(const lb_batch& b, const lb_batch::Class& c, int grid, std::vector<int4>& items,
                      std::vector<int>& starts) {
   struct Brick {
@@ -99,10 +101,8 @@ void build_work_list(const lb_batch& b, const lb_batch::Class& c, int grid, std:
     for (int k = 0; k < p.nbz; ++k)
       for (int j = 0; j < p.nby; ++j)
         for (int i = 0; i < p.nbx; ++i) {
-          const int bxa = std::min(p.bx, x->g.nx - i * p.bx);
-          const int bya = std::min(p.by, x->g.ny - j * p.by);
           const int bz = std::min(p.bz, x->g.nz - k * p.bz);
-          all.push_back({double(bxa) * bya * (bz + p.slots + 2), make_int4(m, i, j, k)});
+          all.push_back({double(p.bx) * p.by * (bz + p.slots + 2), make_int4(m, i, j, k)});
         }
   }
   std::stable_sort(all.begin(), all.end(), [](const Brick& a, const Brick& b2) { return a.cost > b2.cost; });
@@ -216,6 +216,35 @@ int batch_replan(lb_ctx* x) {
   return ctx_replan(x, pick, bz);
 }
 
+// Split the bricks of a class that would not give each of its persistent
+// CTAs at least two: halving its members' sweep length (down to 64 planes)
+// doubles their bricks, so that the static work list balances, at the price
+// of one more pipeline fill (slots + 2 planes) per added brick.  Bits are
+// unchanged.
+int split_for_balance(lb_batch& b, lb_batch::Class& c) {
+  const int occ = c.v->batched_occupancy();
+  if (occ <= 0) return LB_E_CUDA;
+  const int64_t cap = int64_t(k1_sm_count()) * occ;
+  for (int round = 0; round < 8; ++round) {
+    int64_t bricks = 0;
+    for (int m : c.members) {
+      const FusedPlan& p = b.ctxs[m]->plan;
+      bricks += int64_t(p.nbx) * p.nby * p.nbz;
+    }
+    if (bricks >= 2 * cap) return LB_OK;
+    bool changed = false;
+    for (int m : c.members) {
+      lb_ctx* x = b.ctxs[m];
+      if (x->plan.bz <= 64) continue;
+      const int rc = ctx_replan(x, c.v, std::max(64, (x->plan.bz + 1) / 2));
+      if (rc != LB_OK) return rc;
+      changed = true;
+    }
+    if (!changed) return LB_OK;
+  }
+  return LB_OK;
+}
+
 // One step (k = 0 or 1 of the captured pair) of every class.  Classes are
 // independent domains: each runs on its own branch (the batch stream for the
 // first, a side stream forked from it for the others) and all join back.
@@ -310,6 +339,11 @@ int lb_batch_create(lb_ctx* const* ctxs, int32_t n, void* stream, lb_batch** out
         it = b->classes.end() - 1;
       }
       it->members.push_back(i);
+    }
+    if (rc != LB_OK) break;
+    for (auto& c : b->classes) {
+      rc = split_for_balance(*b, c);
+      if (rc != LB_OK) break;
     }
     if (rc != LB_OK) break;
     if (cudaMalloc(reinterpret_cast<void**>(&b->d_status), sizeof(int)) != cudaSuccess) { rc = LB_E_NOMEM; break; }
