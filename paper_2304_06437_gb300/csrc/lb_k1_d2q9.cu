@@ -9,6 +9,7 @@ namespace lbgb {
 
 extern const K1Variant k1_variants_d2q9[] = {
     K1Impl<D2Q9, float, float, 256,1,4,2,0>::variant(LB_D2Q9, LB_F32),
+    K1Impl<D2Q9, float, float, 64,1,4,2,0,0,8>::variant(LB_D2Q9, LB_F32),   // narrow domains (batches), 8 CTAs / SM
     K1Impl<D2Q9, float, float, 64,1,4,2,0>::variant(LB_D2Q9, LB_F32),   // narrow domains (batches)
     K1Impl<D2Q9, double, double, 256,1,3,2,0>::variant(LB_D2Q9, LB_F64),
     K1Impl<D2Q9, __half, float, 256,1,4,2,0>::variant(LB_D2Q9, LB_F16S),

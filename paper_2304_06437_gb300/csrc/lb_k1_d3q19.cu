@@ -13,6 +13,7 @@ extern const K1Variant k1_variants_d3q19[] = {
     K1Impl<D3Q19, float, float, 64,7,3,2,2>::variant(LB_D3Q19, LB_F32),    // + 2 decoupled export warps
     K1Impl<D3Q19, float, float, 64,6,3,2,4>::variant(LB_D3Q19, LB_F32),    // + 4 decoupled export warps
     K1Impl<D3Q19, float, float, 64,8,2,2,0,1>::variant(LB_D3Q19, LB_F32),  // planes stored by TMA
+    K1Impl<D3Q19, float, float, 32,8,2,2,0,0,2>::variant(LB_D3Q19, LB_F32),  // small domains (batches), 2 CTAs / SM
     K1Impl<D3Q19, float, float, 32,8,2,2,0>::variant(LB_D3Q19, LB_F32),  // small domains (batches)
     K1Impl<D3Q19, double, double, 32,8,2,2,0>::variant(LB_D3Q19, LB_F64),
     K1Impl<D3Q19, __half, float, 64,8,4,2,0>::variant(LB_D3Q19, LB_F16S),
