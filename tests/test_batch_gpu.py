@@ -182,3 +182,19 @@ def test_batched_reduction_equals_member_reductions(lb):
         assert all("residual" not in r for r in plain)
     for s in a + b:
         s.close()
+
+
+def test_batched_reduction_flags_only_the_diverged_member(lb):
+    specs = _specs(5)[:4]
+    members = [_make(lb, sp, 800 + i) for i, sp in enumerate(specs)]
+    bad = members[2].get_populations()
+    bad[3, 7] = np.nan
+    members[2].set_populations(bad)
+    with lb.Batch(members) as b:
+        out = b.reduce()
+        assert [r["diverged"] for r in out] == [False, False, True, False]
+        want = [s.reduce() for i, s in enumerate(members) if i != 2]
+        got = [r for i, r in enumerate(out) if i != 2]
+        assert all(g["mass"] == w["mass"] for g, w in zip(got, want))
+    for s in members:
+        s.close()

@@ -200,3 +200,24 @@ def test_tg_d2q9_16384_sampled(Solver):
         rho, u, pi = synth.taylor_green_2d_torch(16384, 0.01, 1.0, 0.8, torch)
         s.init_moments(rho, u, pi)
     check_sampled(Solver, "D2Q9", (16384, 16384), 0.8, "periodic", init, 3, 13)
+
+
+def test_tg_d3q27_1024_sampled(Solver):
+    """D3Q27 periodic Taylor-Green at 1.07e9 nodes (bench.py --workload
+    tg_d3q27_1024: FP32, 116 GB of populations, 32 x 14 bricks)."""
+    def init(s, torch):
+        rho, u, pi = synth.taylor_green_3d_torch(1024, 0.02, 1.0, 0.8, torch)
+        s.init_moments(rho, u, pi)
+        del rho, u, pi
+        torch.cuda.empty_cache()
+    check_sampled(Solver, "D3Q27", (1024, 1024, 1024), 0.8, "periodic", init, 3, 14)
+
+
+def test_tg_d3q27_1024_f16s_sampled(Solver):
+    """The same with shifted FP16 storage (32 x 16 bricks)."""
+    def init(s, torch):
+        rho, u, pi = synth.taylor_green_3d_torch(1024, 0.02, 1.0, 0.8, torch)
+        s.init_moments(rho, u, pi)
+        del rho, u, pi
+        torch.cuda.empty_cache()
+    check_sampled(Solver, "D3Q27", (1024, 1024, 1024), 0.8, "periodic", init, 3, 24, "f16s")
