@@ -17,6 +17,7 @@ extern const K1Variant k1_variants_d3q27[] = {
     K1Impl<D3Q27, __half, float, 32,16,3,2,0>::variant(LB_D3Q27, LB_F16S),  // 16 warps at 128 registers
     K1Impl<D3Q27, __half, float, 32,12,3,2,0>::variant(LB_D3Q27, LB_F16S),
     K1Impl<D3Q27, __half, float, 32,10,3,2,2>::variant(LB_D3Q27, LB_F16S),
+    K1Impl<D3Q27, __nv_bfloat16, float, 32,16,3,2,0>::variant(LB_D3Q27, LB_BF16S),
     K1Impl<D3Q27, __nv_bfloat16, float, 32,12,3,2,0>::variant(LB_D3Q27, LB_BF16S),
 };
 extern const int k1_n_variants_d3q27 = sizeof(k1_variants_d3q27) / sizeof(k1_variants_d3q27[0]);
