@@ -154,12 +154,18 @@ LB_API int lb_get_region(lb_ctx* ctx, const int64_t lo[3], const int64_t size[3]
 /* Enqueues n time steps on the context stream (asynchronous). */
 LB_API int lb_step(lb_ctx* ctx, int64_t n);
 
-/* Density rho [N] and velocity u [d][N] of the stored state (FP64 sums).
+/* Density rho [N] and velocity u [d][N] of the stored state, FP64 results.
+ * FP64 storage sums in FP64; the other storages sum each node's populations
+ * in FP32 carrying the rounding error of every addition in a second FP32 term
+ * (about twice FP32's precision, ~1e-14 of the populations' magnitude), and
+ * convert the two terms to FP64 (GB300 converts and adds FP64 at a small
+ * fraction of its FP32 rate).
  * Either may be NULL.  Host outputs (on_device = 0) are filled a chunk of
  * nodes at a time through one device buffer of at most 512 MB. */
 LB_API int lb_moments(lb_ctx* ctx, double* rho, double* u, int32_t on_device);
 
-/* FP64 on-device reductions over all nodes: total mass sum rho, total momentum
+/* FP64 on-device reductions over all nodes (each node's sums formed as in
+ * lb_moments, accumulated over nodes in FP64): total mass sum rho, total momentum
  * sum_a f_a c_a (without the F/2 shift), and -- if residual is not NULL -- the
  * relative velocity change ||u - u_prev||_2 / ||u||_2 since the previous call
  * that asked for it (1.0 on the first such call, and on the first after the

@@ -6,6 +6,8 @@
 // node is handled by one thread; 64-bit indices throughout.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "lb_dispatch.cuh"
 
 namespace lbgb {
@@ -152,6 +154,58 @@ __global__ void init_kernel(Layout l, S* __restrict__ ft, double rho0, const dou
   }
 }
 
+// Per-node sums drho = sum ft_a and j = sum ft_a c_a of the stored state,
+// returned in FP64.  FP64 storage adds in FP64.  The FP32 arithmetic types
+// (FP32, FP16, BF16 storage) add in FP32 and carry the rounding error of
+// every addition in a second FP32 accumulator (the error-free two-sum; the
+// cascaded summation of Ogita, Rump and Oishi), so that hi + lo is the sum to
+// about twice FP32's precision; only the final pairs are converted to FP64.
+// GB300 converts and adds FP64 at a small fraction of its FP32 rate, which
+// made the plain FP64 path the bound of these kernels.
+struct Sum2 {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
+  }
+  __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
+
+template <class L, class S, class R>
+__device__ __forceinline__ void node_sums(const S* __restrict__ ft, int64_t vol, int64_t o, double& dr, double (&j)[3],
+                                          bool& bad) {
+  if constexpr (std::is_same<R, double>::value) {
+    dr = 0.0;
+    j[0] = j[1] = j[2] = 0.0;
+    static_for<0, L::Q>([&](auto A_) {
+      constexpr int a = decltype(A_)::value;
+      const double v = load_as<S, R>(ft[a * vol + o]);
+      bad |= !isfinite(v);
+      constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+      dr += v;
+      if constexpr (cx != 0) j[0] += cx > 0 ? v : -v;  // zero terms skipped: the sums are unchanged
+      if constexpr (cy != 0) j[1] += cy > 0 ? v : -v;
+      if constexpr (cz != 0) j[2] += cz > 0 ? v : -v;
+    });
+  } else {
+    Sum2 sr, sj[3];
+    static_for<0, L::Q>([&](auto A_) {
+      constexpr int a = decltype(A_)::value;
+      const float v = load_as<S, R>(ft[a * vol + o]);
+      bad |= !isfinite(v);
+      constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+      sr.add(v);
+      if constexpr (cx != 0) sj[0].add(cx > 0 ? v : -v);
+      if constexpr (cy != 0) sj[1].add(cy > 0 ? v : -v);
+      if constexpr (cz != 0) sj[2].add(cz > 0 ? v : -v);
+    });
+    dr = sr.value();
+    for (int k = 0; k < 3; ++k) j[k] = sj[k].value();
+  }
+}
+
 template <class L, class S, class R>
 // nodes [n0, n1) into element idx - n0 of each output component (cs apart)
 __global__ void moments_kernel(Layout l, const S* __restrict__ ft, double rho0, double Fx, double Fy, double Fz,
@@ -160,22 +214,17 @@ __global__ void moments_kernel(Layout l, const S* __restrict__ ft, double rho0, 
   for (int64_t idx = n0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n1;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t o = ioff(l, idx);
-    double dr = 0.0, j[3] = {0.0, 0.0, 0.0};
-    static_for<0, L::Q>([&](auto A_) {
-      constexpr int a = decltype(A_)::value;
-      const double v = static_cast<double>(load_as<S, R>(ft[a * l.vol + o]));
-      constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
-      dr += v;
-      if constexpr (cx != 0) j[0] += cx > 0 ? v : -v;  // zero terms skipped: the sums are unchanged
-      if constexpr (cy != 0) j[1] += cy > 0 ? v : -v;
-      if constexpr (cz != 0) j[2] += cz > 0 ? v : -v;
-    });
+    double dr, j[3];
+    bool bad = false;
+    node_sums<L, S, R>(ft, l.vol, o, dr, j, bad);
     if (rho) rho[idx - n0] = rho0 + dr;
     if (u) {
       const double Fi[3] = {Fx, Fy, Fz};
       for (int k = 0; k < L::D; ++k) {
         const int ax = user_axis<L>(k);
-        u[k * cs + (idx - n0)] = (j[ax] + 0.5 * Fi[ax]) / rho0;
+        // x / 1 is x exactly: the common rho0 = 1 skips the FP64 division
+        const double v = j[ax] + 0.5 * Fi[ax];
+        u[k * cs + (idx - n0)] = rho0 == 1.0 ? v : v / rho0;
       }
     }
   }
@@ -212,18 +261,9 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(Layout l, const S* __r
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < l.n;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t o = ioff(l, idx);
-    double dr = 0.0, j[3] = {0.0, 0.0, 0.0};
+    double dr, j[3];
     bool bad = false;
-    static_for<0, L::Q>([&](auto A_) {
-      constexpr int a = decltype(A_)::value;
-      const double v = static_cast<double>(load_as<S, R>(ft[a * l.vol + o]));
-      bad |= !isfinite(v);
-      constexpr int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
-      dr += v;
-      if constexpr (cx != 0) j[0] += cx > 0 ? v : -v;  // zero terms skipped: the sums are unchanged
-      if constexpr (cy != 0) j[1] += cy > 0 ? v : -v;
-      if constexpr (cz != 0) j[2] += cz > 0 ? v : -v;
-    });
+    node_sums<L, S, R>(ft, l.vol, o, dr, j, bad);
     acc[0] += rho0 + dr;
     acc[1] += j[0];
     acc[2] += j[1];
@@ -231,7 +271,8 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(Layout l, const S* __r
     acc[6] += bad ? 1.0 : 0.0;
     if (residual) {
       for (int k = 0; k < 3; ++k) {
-        const double uk = (j[k] + 0.5 * Fi[k]) / rho0;
+        const double vk = j[k] + 0.5 * Fi[k];
+        const double uk = rho0 == 1.0 ? vk : vk / rho0;  // x / 1 is x exactly
         const double prev = static_cast<double>(uprev[k * l.n + idx]);
         acc[4] += (uk - prev) * (uk - prev);
         acc[5] += uk * uk;
