@@ -282,7 +282,8 @@ typedef struct {
   int32_t bx, by, bz;          /* brick and the sweep length the planner gave the proxy */
   int32_t slots;               /* TMA ring depth */
   int32_t nodes_per_thread;    /* 1 scalar, 2 paired FP32x2 kernel */
-  int32_t export_warps;        /* dedicated shell-export warps (0: shared) */
+  int32_t export_warps;        /* dedicated shell-export warps (0: shared; n > 0 decoupled;
+                                  -n: n warps inside the per-plane barrier) */
   int32_t status;              /* LB_OK, or why this shape could not be timed */
   double ns_per_update;        /* measured time per node update; -1 if not timed */
 } lb_tune_entry;

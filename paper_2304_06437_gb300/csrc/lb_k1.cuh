@@ -50,6 +50,7 @@ struct K1Args {
   Phys<R> ph;
   int nx, ny, nz;
   int64_t pitch, vol;
+  uint32_t vol32;  // vol / 32 (rows are padded to 32 elements)
   int per[3];
   // z faces that border another context's slab (a rank boundary): their
   // incoming shell records sit in ghost slots -- plane -1 / nz of the x and
@@ -111,8 +112,13 @@ __device__ __forceinline__ int lat_slot_of_sub(int ia) {
 template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, int TS = 0, int MINB = 1>
 struct K1Shape {
   static constexpr int Q = L::Q;
-  static constexpr int NTM = BX * BY;        // threads that own a node
-  static constexpr int NT = NTM + 32 * NXW;  // + dedicated export warps
+  static constexpr int NTM = BX * BY;  // threads that own a node
+  // dedicated export warps after the node warps: NXW > 0 of them decoupled
+  // from the node warps' per-plane barrier, or -NXW (NXW < 0) that pass the
+  // same barrier and own no node
+  static constexpr int XW = NXW < 0 ? -NXW : NXW;
+  static constexpr int NT = NTM + 32 * XW;
+  static constexpr int NW = NTM / 32;  // node warps
   static constexpr int NXF = count_dirs<L>(0, 1);
   static constexpr int NYF = count_dirs<L>(1, 1);
   static constexpr int NZF = count_dirs<L>(2, 1);
@@ -132,8 +138,42 @@ struct K1Shape {
   static constexpr int SEGY = NYF > 0 ? (BY + 31) / 32 * 32 : 1;
   static constexpr int SEGX = NYF > 0 ? (BX + 31) / 32 * 32 : 0;
   static constexpr int PE = 2 * SEGY + 2 * SEGX;
-  // export warps: the first NEXW node-owning warps, or NXW dedicated ones
-  static constexpr int NEXW = NXW > 0 ? NXW : (PE + 31) / 32;
+  // export warps: NEXW node-owning warps, or the XW dedicated ones
+  static constexpr int NEXW = NXW != 0 ? XW : (PE + 31) / 32;
+  // shared export warps start at warp EXW0: past the first brick row, whose
+  // warps also stage a whole row of perimeter nodes every plane
+  static constexpr int EXW0 = (NTM / 32 >= NEXW + 4 && BY >= 4) ? 2 : 0;
+  // Which warps export (bit w: warp w).  Shared export warps are spread over
+  // the four schedulers of the SM (warp w issues on scheduler w % 4): each
+  // goes to the scheduler with the least work so far, counting a node warp
+  // as 2 and an export warp's extra work as 1, ties to the lowest free warp.
+  // A CTA of 14 node warps (4, 4, 3, 3 per scheduler) thus puts its four
+  // export warps on the two lighter schedulers.
+  static constexpr uint64_t shared_export_mask() {
+    int load[4] = {0, 0, 0, 0};
+    for (int w = 0; w < NW; ++w) load[w % 4] += 2;
+    uint64_t m = 0;
+    for (int k = 0; k < NEXW; ++k) {
+      int best = -1;
+      for (int w = EXW0; w < NW; ++w) {
+        if ((m >> w) & 1) continue;
+        if (best < 0 || load[w % 4] < load[best % 4]) best = w;
+      }
+      if (best < 0) break;
+      m |= uint64_t(1) << best;
+      load[best % 4] += 1;
+    }
+    return m;
+  }
+  static constexpr uint64_t EXMASK =
+      NXW != 0 ? (((uint64_t(1) << XW) - 1) << NW) : shared_export_mask();
+  // the lowest export warp, and whether the export warps are consecutive
+  static constexpr int EXFIRST = [] {
+    int w = 0;
+    while (w < 63 && !((EXMASK >> w) & 1)) ++w;
+    return w;
+  }();
+  static constexpr bool EXCONTIG = (EXMASK >> EXFIRST) == (uint64_t(1) << NEXW) - 1;
   // stage row of one perimeter node: Q values padded so that the row is a
   // whole, odd number of 16-byte units (vector stores, conflict-free loads)
   static constexpr int VEC = 16 / int(sizeof(R));
@@ -170,7 +210,8 @@ struct K1Shape {
   static constexpr bool UNROLL3 = (Q * sizeof(R) <= 76 || (Q * sizeof(R) <= 108 && NT * MINB <= 256));
   static_assert(SMEM <= SMEM_CAP, "shared memory of the shape exceeds its share of the SM");
   static_assert(BY == 1 || NYF > 0, "a 2D brick has one internal row");
-  static_assert(NXW > 0 || 32 * NEXW <= NTM, "export entries need more warps than the CTA has");
+  static_assert(NXW != 0 || 32 * NEXW <= NTM, "export entries need more warps than the CTA has");
+  static_assert(NTM % 32 == 0 && NW + XW <= 32, "node threads fill whole warps");
   static_assert(WB == 1 || WB == 2, "one or two window buffers");
 };
 
@@ -537,11 +578,19 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
   // perimeter (lateral boundary) slot of this node, and export-warp work
   const int pidx = active ? perimeter_index<NYF>(tx, ty, bxa, bya) : -1;
   const bool any_lateral_export = nbW || nbE || (NYF > 0 && (nbS || nbN));
-  // shared export warps start at warp EXW0: past the first brick row, whose
-  // warps also stage a whole row of perimeter nodes every plane
-  constexpr int EXW0 = (NXW == 0 && NTM / 32 >= NEXW + 4 && BY >= 4) ? 2 : 0;
-  const bool exp_warp = any_lateral_export && (NXW > 0 ? !is_main : (warp >= EXW0 && warp < EXW0 + NEXW));
-  const int exp_lane = NXW > 0 ? tid - NTM : (warp - EXW0) * 32 + lane;  // first export entry of this lane
+  // export warps take the entries in warp order; exp_lane is this lane's first
+  bool exp_warp;
+  int exp_lane;
+  if constexpr (NXW > 0) {
+    exp_warp = any_lateral_export && !is_main;
+    exp_lane = tid - NTM;
+  } else if constexpr (Sh::EXCONTIG) {
+    exp_warp = any_lateral_export && warp >= Sh::EXFIRST && warp < Sh::EXFIRST + NEXW;
+    exp_lane = (warp - Sh::EXFIRST) * 32 + lane;
+  } else {
+    exp_warp = any_lateral_export && ((Sh::EXMASK >> warp) & 1);
+    exp_lane = __popcll(Sh::EXMASK & ((uint64_t(1) << warp) - 1)) * 32 + lane;
+  }
 
   // this thread's own cell in the window (interior of the padding ring)
   const int wbase = (ty + PY) * WX + (tx + 1);
@@ -906,7 +955,7 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
 // One launch per time step of one domain: one CTA per brick column.
 template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE, int TS = 0,
           bool LINK = false, int MINB = 1>
-__global__ void __launch_bounds__(BX* BY + 32 * NXW, MINB)
+__global__ void __launch_bounds__(K1Shape<L, S, R, BX, BY, NS, WB, NXW, TS, MINB>::NT, MINB)
     k1_fused_step(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ K1Args<R> args) {
   const int nbx = args.nbx, nby = args.nby;
   const int b = blockIdx.x;
@@ -921,7 +970,7 @@ __global__ void __launch_bounds__(BX* BY + 32 * NXW, MINB)
 // (dom_par[d] + k) & 1.
 template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE, int TS = 0,
           int MINB = 1>
-__global__ void __launch_bounds__(BX* BY + 32 * NXW, MINB)
+__global__ void __launch_bounds__(K1Shape<L, S, R, BX, BY, NS, WB, NXW, TS, MINB>::NT, MINB)
     k1_batched_step(const K1Args<R>* __restrict__ args, int n_dom, const CUtensorMap* __restrict__ tmaps,
                     const int4* __restrict__ items, const int* __restrict__ starts, const int* __restrict__ dom_par,
                     int k) {

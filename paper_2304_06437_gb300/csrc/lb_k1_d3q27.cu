@@ -1,6 +1,7 @@
 // lb_k1_d3q27.cu -- compiled brick shapes of the fused step for D3Q27.
 // Each entry: storage / arithmetic type, brick bx x by, TMA pipeline depth,
-// window buffers, dedicated export warps.  The first entry of a storage type
+// window buffers, dedicated export warps (negative: -n warps that pass the
+// node warps' per-plane barrier; positive: decoupled through a staged ring).  The first entry of a storage type
 // is the default; the others are alternatives the planner can be asked for
 // (by brick shape, LB_FUSED_PIPELINE, the autotuner or a batch).
 #include "lb_k1_launch.cuh"
@@ -8,7 +9,9 @@
 namespace lbgb {
 
 extern const K1Variant k1_variants_d3q27[] = {
-    K1Impl<D3Q27, float, float, 32,14,2,2,0>::variant(LB_D3Q27, LB_F32),  // 14 warps at 128 registers
+    // 14 node warps + 2 export warps in the barrier, 128 registers
+    K1Impl<D3Q27, float, float, 32,14,2,2,-2>::variant(LB_D3Q27, LB_F32),
+    K1Impl<D3Q27, float, float, 32,14,2,2,0>::variant(LB_D3Q27, LB_F32),  // node warps export
     K1Impl<D3Q27, float, float, 32,12,2,2,0>::variant(LB_D3Q27, LB_F32),
     K1Impl<D3Q27, float, float, 32,10,2,2,2>::variant(LB_D3Q27, LB_F32),  // + 2 decoupled export warps
     K1Impl<D3Q27, float, float, 32,10,3,2,0>::variant(LB_D3Q27, LB_F32),  // deeper TMA ring

@@ -43,7 +43,7 @@ static int variant_lists(int lattice, const K1Variant* lists[2], int counts[2]) 
 }
 
 // The first compiled shape that matches (lattice, storage, bx, by, ns, wb,
-// nxw, npt, ts, minb); zero fields (negative nxw, ts) match anything.
+// nxw, npt, ts, minb); zero fields (-1 for nxw and ts) match anything.
 static const K1Variant* find_variant(int lattice, int storage, int bx, int by, int ns, int wb, int nxw, int npt,
                                      int ts, int minb = 0) {
   const K1Variant* lists[2];
@@ -57,7 +57,7 @@ static const K1Variant* find_variant(int lattice, int storage, int bx, int by, i
       if (by > 0 && v.by != by) continue;
       if (ns > 0 && v.ns != ns) continue;
       if (wb > 0 && v.wb != wb) continue;
-      if (nxw >= 0 && v.nxw != nxw) continue;
+      if (nxw != -1 && v.nxw != nxw) continue;
       if (npt > 0 && v.npt != npt) continue;
       if (ts >= 0 && v.ts != ts) continue;
       if (minb > 0 && v.minb != minb) continue;
@@ -69,9 +69,9 @@ static const K1Variant* find_variant(int lattice, int storage, int bx, int by, i
 
 // Optional pipeline request from the environment,
 // "NS,WB[,NXW[,NPT[,TS[,MINB]]]]" (TMA slots, window buffers, dedicated
-// export warps, nodes per thread, TMA store of completed planes, CTAs per
-// SM), used to compare the compiled alternatives of a brick shape; 0 (-1 for
-// NXW and TS) = any.
+// export warps (negative: warps inside the per-plane barrier), nodes per
+// thread, TMA store of completed planes, CTAs per SM), used to compare the
+// compiled alternatives of a brick shape; 0 (-1 for NXW and TS) = any.
 static void pipeline_request(int* ns, int* wb, int* nxw, int* npt, int* ts, int* minb) {
   *ns = 0;
   *wb = 0;

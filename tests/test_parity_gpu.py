@@ -116,6 +116,36 @@ def test_decoupled_export_warps_bitwise(Solver, lat, tile, storage, fname):
     assert np.array_equal(outs[0], outs[2])
 
 
+@pytest.mark.parametrize("lat,tile,storage,slots", [("D3Q27", (32, 14, 4), "f32", 2), ("D3Q19", (32, 14, 5), "f32", 3),
+                                                    ("D3Q19", (64, 7, 5), "f16s", 4)])
+@pytest.mark.parametrize("fname", ["lid", "periodic", "duct"])
+def test_barrier_export_warps_bitwise(Solver, lat, tile, storage, slots, fname, monkeypatch):
+    """Brick shapes with two dedicated export warps that own no node but pass
+    the node warps' per-plane barrier (selected by a negative export-warp
+    field of the pipeline request) give the two-pass bits, on grids of many
+    ragged bricks and ring laps."""
+    from paper_2304_06437_gb300.solver import fused_plan
+    dims = (150, 30, 23) if lat == "D3Q19" else (70, 33, 13)
+    faces, wall_u = faces_for(lat, fname)
+    force = (2e-5, 0, 1e-5) if fname == "duct" else (0, 0, 0)
+    f0 = random_state(lat, dims, 79)
+    outs = []
+    for scheme, t in (("two_pass", None), ("fused", tile), ("fused", (tile[0], tile[1], 0))):
+        if scheme == "fused":
+            monkeypatch.setenv("LB_FUSED_PIPELINE", "%d,2,-2" % slots)
+            assert fused_plan(lat, dims, storage, t)["export_warps"] == -2
+        s = Solver(lat, dims, 0.58, faces=faces, wall_u=wall_u, storage=storage, scheme=scheme, force=force, tile=t)
+        monkeypatch.delenv("LB_FUSED_PIPELINE", raising=False)
+        if scheme == "fused":
+            assert s.info()["tile"][:2] == tile[:2] and s.info()["tma_slots"] == slots
+        s.set_populations(np.ascontiguousarray(f0))
+        s.step(9)
+        outs.append(s.get_populations())
+        s.close()
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+
+
 @pytest.mark.parametrize("lat", ["D3Q19", "D3Q27"])
 def test_sweep_length_invariance(Solver, lat):
     """Every brick split along z gives the same bits (a race would not)."""

@@ -100,3 +100,21 @@ def test_tile_requests_and_rejections(P):
         args.update(bad)
         with pytest.raises((LBError, KeyError)):
             P.fused_plan(args["lat"], args["dims"], args["storage"])
+
+
+def test_pipeline_request_selects_export_warp_variants(P, monkeypatch):
+    """The export-warp field of LB_FUSED_PIPELINE picks among the compiled
+    alternatives of a brick: 2 decoupled warps, 2 warps inside the per-plane
+    barrier (-2), or none (node warps export); -1 takes the shape's default."""
+    cases = [("D3Q27", "f32", (32, 14, 0), "2,2,-2", -2), ("D3Q27", "f32", (32, 14, 0), "2,2,-1", -2),
+             ("D3Q27", "f32", (32, 14, 0), "2,2,0", 0),
+             ("D3Q27", "f32", (32, 10, 0), "2,2,2", 2), ("D3Q19", "f16s", (64, 7, 0), "4,2,-2", -2),
+             ("D3Q19", "f16s", (64, 7, 0), "4,2,2", 2), ("D3Q19", "f32", (32, 14, 0), "3,2,-2", -2)]
+    for lat, storage, tile, req, want in cases:
+        monkeypatch.setenv("LB_FUSED_PIPELINE", req)
+        p = P.fused_plan(lat, (256, 256, 256), storage, tile=tile, sms=152)
+        assert p["export_warps"] == want and (p["bx"], p["by"]) == tile[:2], (lat, req, p)
+        _check(lat, (256, 256, 256), p)
+    monkeypatch.delenv("LB_FUSED_PIPELINE")
+    assert P.fused_plan("D3Q27", (256, 256, 256), "f32", tile=(32, 14, 0), sms=152)["export_warps"] == -2
+    assert P.fused_plan("D3Q19", (256, 256, 256), "f32", sms=152)["export_warps"] == 0
