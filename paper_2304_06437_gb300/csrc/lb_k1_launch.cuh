@@ -51,6 +51,7 @@ K1Args<R> k1_make_args(lb_ctx* ctx, int cur_parity, int next_parity) {
   a.nz = g.nz;
   a.pitch = g.pitch;
   a.vol = g.vol;
+  a.vol32 = uint32_t(g.vol / 32);
   for (int k = 0; k < 3; ++k) a.per[k] = g.per[k];
   a.zlink[0] = g.zlink[0];
   a.zlink[1] = g.zlink[1];
