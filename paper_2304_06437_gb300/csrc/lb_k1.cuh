@@ -209,10 +209,11 @@ struct K1Shape {
   // FP32 arithmetic values per node, or 27 in a CTA of at most 256 threads
   static constexpr bool UNROLL3 = (Q * sizeof(R) <= 76 || (Q * sizeof(R) <= 108 && NT * MINB <= 256));
   // 16-bit storage addresses each population store as one wide multiply-add
-  // of vol / 32 by a constant (measured 8-11 % faster for FP16 / BF16
-  // storage); FP32 / FP64 storage walks one pointer along the directions
-  // (the multiply-add form measured 2 % slower for D3Q19 FP32)
-  static constexpr bool WIDE_STORE = sizeof(S) == 2;
+  // of vol / 32 by a constant; the others walk one pointer along the
+  // directions.  Measured at 1024^3 on one GPU, multiply-add against pointer
+  // walk: D3Q27 FP16 30.3 / 28.8, D3Q19 BF16 37.5 / 36.5, but D3Q19 FP16
+  // 39.5 / 40.4 and D3Q19 FP32 35.3 / 36.1 GLUPS, so those keep the walk
+  static constexpr bool WIDE_STORE = sizeof(S) == 2 && !(Q == 19 && std::is_same<S, __half>::value);
   static_assert(SMEM <= SMEM_CAP, "shared memory of the shape exceeds its share of the SM");
   static_assert(BY == 1 || NYF > 0, "a 2D brick has one internal row");
   static_assert(NXW != 0 || 32 * NEXW <= NTM, "export entries need more warps than the CTA has");

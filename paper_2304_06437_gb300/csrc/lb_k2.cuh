@@ -554,19 +554,37 @@ __device__ __forceinline__ bool k2_brick(const CUtensorMap* tmap_p, const K1Args
     // plane g - 1 is complete: store, stage its perimeter, export along z
     const int zd = g - 1;
     if (act0 && zd >= z0 && zd < z1) {
-      S* p = fglob + (x + args.pitch * (y + int64_t(ny) * zd));
-      if (act1) {
-        static_for<0, Q>([&](auto A_) {
-          constexpr int a = decltype(A_)::value;
-          store_pair<S>(p, G0[a]);
-          p += args.vol;
-        });
+      if constexpr (sizeof(S) == 2) {
+        // 16-bit storage: direction a lies a * vol elements further, one wide
+        // multiply-add of vol / 32 (rows are padded to 32 elements) per store
+        char* p = reinterpret_cast<char*>(fglob + (x + args.pitch * (y + int64_t(ny) * zd)));
+        const uint32_t v32 = args.vol32;
+        if (act1) {
+          static_for<0, Q>([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            store_pair<S>(reinterpret_cast<S*>(p + uint64_t(v32) * uint32_t(a * 32 * sizeof(S))), G0[a]);
+          });
+        } else {
+          static_for<0, Q>([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            *reinterpret_cast<S*>(p + uint64_t(v32) * uint32_t(a * 32 * sizeof(S))) = store_as<S, R>(G0[a].x);
+          });
+        }
       } else {
-        static_for<0, Q>([&](auto A_) {
-          constexpr int a = decltype(A_)::value;
-          *p = store_as<S, R>(G0[a].x);
-          p += args.vol;
-        });
+        S* p = fglob + (x + args.pitch * (y + int64_t(ny) * zd));
+        if (act1) {
+          static_for<0, Q>([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            store_pair<S>(p, G0[a]);
+            p += args.vol;
+          });
+        } else {
+          static_for<0, Q>([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            *p = store_as<S, R>(G0[a].x);
+            p += args.vol;
+          });
+        }
       }
       if (any_lateral_export) {
 #pragma unroll
