@@ -359,7 +359,9 @@ def main():
     avg_launch_s = float(np.mean(per_launch)) * 1e-3
     peak, peak_kind = read_peaks()
     achieved = alg_bytes / avg_launch_s / 1e9
-    traffic_per_update = read_traffic("%s_%s_%s" % (args.scheme, lattice, args.storage))
+    # ncu bytes of the default brick shape: not for a requested brick or pipeline
+    default_shape = args.tile is None and not os.environ.get("LB_FUSED_PIPELINE")
+    traffic_per_update = read_traffic("%s_%s_%s" % (args.scheme, lattice, args.storage)) if default_shape else None
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
         "peak_kind": peak_kind,
