@@ -151,7 +151,14 @@ LB_API int lb_get_populations(lb_ctx* ctx, double* f, int32_t on_device);
  * laid out [q][size_z][size_y][size_x].  For sampled checks on large grids. */
 LB_API int lb_get_region(lb_ctx* ctx, const int64_t lo[3], const int64_t size[3], double* f_host);
 
-/* Enqueues n time steps on the context stream (asynchronous). */
+/* Enqueues n time steps on the context stream (asynchronous).  Each step is
+ * one application of the step of section 3 (Eq. LBexp with fhat^neq, the
+ * multline step equation) with the walls of section 5.1.  For n >= 4 the
+ * fused scheme launches a pair of steps captured once as a CUDA graph (held
+ * by the context until it is re-planned or destroyed); if the caller is
+ * capturing the context stream, the steps are launched one by one and land
+ * in the caller's graph.  Errors: LB_E_INVAL (n < 0, or n > 1 on a slab with
+ * a link face), LB_E_CUDA (a launch failed). */
 LB_API int lb_step(lb_ctx* ctx, int64_t n);
 
 /* Density rho [N] and velocity u [d][N] of the stored state, FP64 results.

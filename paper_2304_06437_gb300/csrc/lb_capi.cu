@@ -173,12 +173,19 @@ struct DeviceGuard {
 
 namespace lbgb {
 
+void drop_step_graph(lb_ctx* ctx) {
+  if (ctx->step_graph) cudaGraphExecDestroy(ctx->step_graph);
+  ctx->step_graph = nullptr;
+}
+
 int ctx_replan(lb_ctx* ctx, const void* variant, int bz) {
   if (!ctx || ctx->scheme != LB_SCHEME_FUSED) return LB_E_INVAL;
   FusedPlan p;
   if (!k1_plan_variant(ctx->g, variant, bz, &p)) return LB_E_INVAL;
   DeviceGuard guard(ctx->device);
   LB_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+  // a captured step pair holds the old shell buffers and brick plan
+  drop_step_graph(ctx);
   const size_t aux_bytes = size_t(2) * size_t(p.parity_elems) * ctx->real_bytes;
   void* aux = nullptr;
   LB_TRY_CUDA(cudaMalloc(&aux, aux_bytes));
@@ -469,6 +476,7 @@ void lb_destroy(lb_ctx* ctx) {
   if (!ctx) return;
   DeviceGuard guard(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  drop_step_graph(ctx);
   if (ctx->f) cudaFree(ctx->f);
   if (ctx->aux) cudaFree(ctx->aux);
   if (ctx->d_status) cudaFree(ctx->d_status);
@@ -608,12 +616,64 @@ int lb_get_region(lb_ctx* ctx, const int64_t lo[3], const int64_t size[3], doubl
                   &ra);
 }
 
+// Record two fused steps, from the current shell parity, as a CUDA graph on
+// the context stream (nothing runs).  Returns false, leaving no error set,
+// where the stream cannot be captured (it is already being captured, e.g. by
+// the caller) or capture fails; lb_step then launches step by step.
+static bool capture_step_pair(lb_ctx* ctx) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return false;
+  }
+  const int p0 = ctx->parity;
+  if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaError_t e = k1_step(ctx);
+  if (e == cudaSuccess) e = k1_step(ctx);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(ctx->stream, &graph);
+  ctx->parity = p0;  // the pair was only recorded
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess && ee == cudaSuccess && graph) e = cudaGraphInstantiate(&exec, graph, 0);
+  else e = cudaErrorStreamCaptureInvalidated;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+  if (e != cudaSuccess || !exec) return false;
+  ctx->step_graph = exec;
+  ctx->graph_parity = p0;
+  return true;
+}
+
 int lb_step(lb_ctx* ctx, int64_t n) {
   if (!ctx || n < 0) return LB_E_INVAL;
   // a slab bordering others takes one step between two halo exchanges
   if (n > 1 && (ctx->g.zlink[0] || ctx->g.zlink[1])) return LB_E_INVAL;
   DeviceGuard guard(ctx->device);
-  for (int64_t i = 0; i < n; ++i) {
+  int64_t i = 0;
+  // long runs of the fused scheme replay a captured pair of steps: one graph
+  // launch per two steps instead of two launches, each with its host-side
+  // argument set-up (what dominates the step of a small domain)
+  constexpr int64_t kGraphMinSteps = 4;
+  if (ctx->scheme == LB_SCHEME_FUSED && n >= kGraphMinSteps) {
+    if (ctx->step_graph && ctx->parity != ctx->graph_parity) {
+      // the pair starts from the other parity: one plain step first
+      cudaError_t e = k1_step(ctx);
+      if (e != cudaSuccess) return cuda_status(e);
+      ctx->steps_done++;
+      ++i;
+    }
+    if (ctx->step_graph || capture_step_pair(ctx)) {
+      for (; i + 2 <= n; i += 2) {
+        cudaError_t e = cudaGraphLaunch(ctx->step_graph, ctx->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        ctx->steps_done += 2;
+      }
+    }
+  }
+  for (; i < n; ++i) {
     cudaError_t e = ctx->scheme == LB_SCHEME_FUSED ? k1_step(ctx) : k0_step(ctx);
     if (e != cudaSuccess) return cuda_status(e);
     ctx->steps_done++;

@@ -73,6 +73,11 @@ struct lb_ctx {
   float* d_uprev;         // residual snapshot, allocated on first use
   bool have_uprev;
   int64_t steps_done;
+  // two fused steps captured as a CUDA graph from shell parity graph_parity
+  // (lb_step replays it for long runs; null until first needed, dropped when
+  // the brick plan or the shell buffers change)
+  cudaGraphExec_t step_graph = nullptr;
+  int graph_parity = 0;
 };
 
 namespace lbgb {
@@ -94,6 +99,8 @@ int k1_variants_for(int lattice, int storage, const void** out, int cap);
 // (bz = 0: the planner's choice): new shell buffers and TMA descriptor, shell
 // rebuilt from the current populations (lb_capi.cu)
 int ctx_replan(lb_ctx* ctx, const void* variant, int bz = 0);
+// release the captured step pair of lb_step (plan or shell buffers change)
+void drop_step_graph(lb_ctx* ctx);
 cudaError_t k1_step(lb_ctx* ctx);
 cudaError_t k1_bootstrap(lb_ctx* ctx);  // fill the current shell parity from f
 cudaError_t k1_configure(lb_ctx* ctx);  // one-time kernel attributes
