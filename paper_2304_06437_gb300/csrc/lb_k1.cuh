@@ -985,19 +985,45 @@ __global__ void __launch_bounds__(K1Shape<L, S, R, BX, BY, NS, WB, NXW, TS, MINB
 // (domain, bI, bJ, bK); the arguments of domain d at shell parity p are
 // args[p * n_dom + d], and domain d's parity at this launch is
 // (dom_par[d] + k) & 1.
+// dynamic shared memory of the batched launch: the brick's own buffers, then
+// the current member's arguments where they fit (else read from global memory)
+template <class Sh, class R>
+struct K1BatchSmem {
+  static constexpr size_t ARGS = (sizeof(K1Args<R>) + 15) / 16 * 16;
+  static constexpr bool STAGED = Sh::SMEM + ARGS <= Sh::SMEM_CAP;
+  static constexpr size_t BYTES = Sh::SMEM + (STAGED ? ARGS : 0);
+};
+
 template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE, int TS = 0,
           int MINB = 1>
 __global__ void __launch_bounds__(K1Shape<L, S, R, BX, BY, NS, WB, NXW, TS, MINB>::NT, MINB)
     k1_batched_step(const K1Args<R>* __restrict__ args, int n_dom, const CUtensorMap* __restrict__ tmaps,
                     const int4* __restrict__ items, const int* __restrict__ starts, const int* __restrict__ dom_par,
                     int k) {
+  using Sh = K1Shape<L, S, R, BX, BY, NS, WB, NXW, TS, MINB>;
+  using BS = K1BatchSmem<Sh, R>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  K1Args<R>* sa = reinterpret_cast<K1Args<R>*>(smem + Sh::SMEM);
   const int i1 = starts[blockIdx.x + 1];
   for (int i = starts[blockIdx.x]; i < i1; ++i) {
     const int4 it = items[i];
     const int p = (dom_par[it.x] + k) & 1;
-    if (!k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE, TS, false, MINB>(tmaps + it.x, args[size_t(p) * n_dom + it.x], it.y,
-                                                           it.z, it.w))
-      return;
+    const K1Args<R>& ga = args[size_t(p) * n_dom + it.x];
+    if constexpr (BS::STAGED) {
+      // the sweep reads its arguments (physical constants, strides, shell
+      // offsets) every plane: from shared memory they are plain shared loads
+      // instead of global loads the compiler cannot keep in registers.  The
+      // previous brick ended on a CTA barrier, so no thread still reads sa.
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(&ga);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(sa);
+      for (int w = threadIdx.x; w < int(sizeof(K1Args<R>) / 4); w += blockDim.x) dst[w] = src[w];
+      __syncthreads();
+      if (!k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE, TS, false, MINB>(tmaps + it.x, *sa, it.y, it.z, it.w))
+        return;
+    } else {
+      if (!k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE, TS, false, MINB>(tmaps + it.x, ga, it.y, it.z, it.w))
+        return;
+    }
   }
 }
 

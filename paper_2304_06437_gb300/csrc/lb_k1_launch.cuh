@@ -130,19 +130,21 @@ struct K1Impl {
     return cudaGetLastError();
   }
 
+  static constexpr size_t SMEM_B = K1BatchSmem<Sh, R>::BYTES;
+
   static cudaError_t batched(const BatchLaunch& b, cudaStream_t stream) {
     const K1Args<R>* args = static_cast<const K1Args<R>*>(b.args);
     if (b.force)
-      k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true, TS, MINB><<<b.grid, Sh::NT, Sh::SMEM, stream>>>(
+      k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true, TS, MINB><<<b.grid, Sh::NT, SMEM_B, stream>>>(
           args, b.n_dom, b.tmaps, b.items, b.starts, b.dom_par, b.k);
     else
-      k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, false, TS, MINB><<<b.grid, Sh::NT, Sh::SMEM, stream>>>(
+      k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, false, TS, MINB><<<b.grid, Sh::NT, SMEM_B, stream>>>(
           args, b.n_dom, b.tmaps, b.items, b.starts, b.dom_par, b.k);
     return cudaGetLastError();
   }
 
   static int batched_occupancy() {
-    const int sm = int(Sh::SMEM);
+    const int sm = int(SMEM_B);
     if (configure() != cudaSuccess) return 0;
     if (cudaFuncSetAttribute(k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, false, TS, MINB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
@@ -151,7 +153,7 @@ struct K1Impl {
       return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k1_batched_step<L, S, R, BX, BY, NS, WB, NXW, true, TS, MINB>, Sh::NT,
-                                                      Sh::SMEM) != cudaSuccess)
+                                                      SMEM_B) != cudaSuccess)
       return 0;
     return n;
   }

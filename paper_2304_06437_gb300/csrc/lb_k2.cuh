@@ -54,6 +54,7 @@ struct K2Shape {
   static constexpr size_t OFF_DESC = OFF_STAGE + align128(2 * STAGE);
   static constexpr size_t OFF_BAR = OFF_DESC + align128(size_t(PMAX) * 24);
   static constexpr size_t SMEM = OFF_BAR + align128(NS * sizeof(uint64_t));
+  static constexpr size_t SMEM_CAP = size_t(228) * 1024 - 1024;
   static_assert(BX % 2 == 0, "pairs need an even brick width");
   static_assert(WX % 2 == 0 && WPLANE % 2 == 0, "pair cells must stay 8-byte aligned");
   static_assert(BY == 1 || NYF > 0, "a 2D brick has one internal row");
@@ -689,11 +690,26 @@ __global__ void __launch_bounds__(BX* BY / 2, 1)
     k2_batched_step(const K1Args<float>* __restrict__ args, int n_dom, const CUtensorMap* __restrict__ tmaps,
                     const int4* __restrict__ items, const int* __restrict__ starts, const int* __restrict__ dom_par,
                     int k) {
+  using Sh = K2Shape<L, S, BX, BY, NS>;
+  using BS = K1BatchSmem<Sh, float>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  K1Args<float>* sa = reinterpret_cast<K1Args<float>*>(smem + Sh::SMEM);
   const int i1 = starts[blockIdx.x + 1];
   for (int i = starts[blockIdx.x]; i < i1; ++i) {
     const int4 it = items[i];
     const int p = (dom_par[it.x] + k) & 1;
-    if (!k2_brick<L, S, BX, BY, NS, FORCE>(tmaps + it.x, args[size_t(p) * n_dom + it.x], it.y, it.z, it.w)) return;
+    const K1Args<float>& ga = args[size_t(p) * n_dom + it.x];
+    if constexpr (BS::STAGED) {
+      // the member's arguments as shared loads in the sweep (see
+      // k1_batched_step); the previous brick ended on a CTA barrier
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(&ga);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(sa);
+      for (int w = threadIdx.x; w < int(sizeof(K1Args<float>) / 4); w += blockDim.x) dst[w] = src[w];
+      __syncthreads();
+      if (!k2_brick<L, S, BX, BY, NS, FORCE>(tmaps + it.x, *sa, it.y, it.z, it.w)) return;
+    } else {
+      if (!k2_brick<L, S, BX, BY, NS, FORCE>(tmaps + it.x, ga, it.y, it.z, it.w)) return;
+    }
   }
 }
 
@@ -701,6 +717,7 @@ __global__ void __launch_bounds__(BX* BY / 2, 1)
 template <class L, class S, int BX, int BY, int NS>
 struct K2Impl {
   using Sh = K2Shape<L, S, BX, BY, NS>;
+  static constexpr size_t SMEM_B = K1BatchSmem<Sh, float>::BYTES;
 
   static cudaError_t configure() {
     const int sm = int(Sh::SMEM);
@@ -716,10 +733,10 @@ struct K2Impl {
                              sm);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k2_batched_step<L, S, BX, BY, NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             sm);
+                             int(SMEM_B));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k2_batched_step<L, S, BX, BY, NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                sm);
+                                int(SMEM_B));
   }
 
   static cudaError_t step(lb_ctx* ctx) {
@@ -743,11 +760,11 @@ struct K2Impl {
   static cudaError_t batched(const BatchLaunch& b, cudaStream_t stream) {
     const K1Args<float>* args = static_cast<const K1Args<float>*>(b.args);
     if (b.force)
-      k2_batched_step<L, S, BX, BY, NS, true><<<b.grid, Sh::NT, Sh::SMEM, stream>>>(args, b.n_dom, b.tmaps, b.items,
-                                                                                   b.starts, b.dom_par, b.k);
+      k2_batched_step<L, S, BX, BY, NS, true><<<b.grid, Sh::NT, SMEM_B, stream>>>(args, b.n_dom, b.tmaps, b.items,
+                                                                                 b.starts, b.dom_par, b.k);
     else
-      k2_batched_step<L, S, BX, BY, NS, false><<<b.grid, Sh::NT, Sh::SMEM, stream>>>(args, b.n_dom, b.tmaps, b.items,
-                                                                                    b.starts, b.dom_par, b.k);
+      k2_batched_step<L, S, BX, BY, NS, false><<<b.grid, Sh::NT, SMEM_B, stream>>>(args, b.n_dom, b.tmaps, b.items,
+                                                                                  b.starts, b.dom_par, b.k);
     return cudaGetLastError();
   }
 
@@ -755,7 +772,7 @@ struct K2Impl {
     int n = 0;
     if (configure() != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k2_batched_step<L, S, BX, BY, NS, true>, Sh::NT,
-                                                      Sh::SMEM) != cudaSuccess)
+                                                      SMEM_B) != cudaSuccess)
       return 0;
     return n;
   }
