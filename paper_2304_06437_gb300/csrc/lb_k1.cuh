@@ -350,7 +350,7 @@ __device__ __forceinline__ int export_seg_start(int face) {
 // and export the populations that leave through one face; dst is the node's
 // record of that face in this plane, stride the distance between directions.
 template <class L, class S, class R, bool FORCE>
-__device__ __forceinline__ void export_one_face(const K1Args<R>& args, const R (&fin)[L::Q], int face, R* dst,
+__device__ __forceinline__ void export_one_face(const Phys<R>& ph, const R (&fin)[L::Q], int face, R* dst,
                                                 int64_t stride) {
   R fr[L::Q];
   static_for<0, L::Q>([&](auto A_) {
@@ -358,9 +358,9 @@ __device__ __forceinline__ void export_one_face(const K1Args<R>& args, const R (
     fr[a] = round_to_storage<S, R>(fin[a]);
   });
   Mom<R> m;
-  moments<L, R, FORCE>(fr, args.ph, m);
+  moments<L, R, FORCE>(fr, ph, m);
   Coef<R> kc;
-  coeffs<L, R, FORCE>(m, args.ph, kc);
+  coeffs<L, R, FORCE>(m, ph, kc);
   if (face == 0) export_face<L, R, 0, -1>(kc, {dst, stride});
   else if (face == 1) export_face<L, R, 0, 1>(kc, {dst, stride});
   if constexpr (count_dirs<L>(1, 1) > 0) {
@@ -377,8 +377,12 @@ __device__ __forceinline__ void export_one_face(const K1Args<R>& args, const R (
 //
 // LINK: compiled for contexts with a link face (slab decomposition); the
 // other instantiations compile the plain form, whose shell has no ghosts.
+//
+// PHPLANE: the arguments sit in shared memory (batched sweeps); the collision
+// then reads its physical constants as one block copy at the start of each
+// use (loads issued ahead of the collision, not one per operand inside it).
 template <class L, class S, class R, int BX, int BY, int NS, int WB, int NXW, bool FORCE, int TS = 0,
-          bool LINK = false, int MINB = 1>
+          bool LINK = false, int MINB = 1, bool PHPLANE = false>
 __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args<R>& args, const int bI,
                                          const int bJ, const int bK) {
   using Sh = K1Shape<L, S, R, BX, BY, NS, WB, NXW, TS, MINB>;
@@ -641,8 +645,14 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
         for (int a = 0; a < Q; ++a) fq[a] = fin[a];
         const int face = export_face_of<Sh>(e);
         const bool xface = face < 2;
-        export_one_face<L, S, R, FORCE>(args, fq, face, shn + desc_off[e] + int64_t(zx) * (xface ? ny : nx),
-                                        xface ? nzy : nzx);
+        if constexpr (PHPLANE) {
+          const Phys<R> phl = args.ph;
+          export_one_face<L, S, R, FORCE>(phl, fq, face, shn + desc_off[e] + int64_t(zx) * (xface ? ny : nx),
+                                          xface ? nzy : nzx);
+        } else {
+          export_one_face<L, S, R, FORCE>(args.ph, fq, face, shn + desc_off[e] + int64_t(zx) * (xface ? ny : nx),
+                                          xface ? nzy : nzx);
+        }
       }
     }
   };
@@ -656,6 +666,8 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
     if (real) {
       const int k = c - z0;
       const int slot = k % NS;
+      Phys<R> phl;
+      if constexpr (PHPLANE) phl = args.ph;  // loads in flight during the wait
       if (!mbar_wait_bounded(&bars[slot], (k / NS) & 1, kWaitLimitNs)) return false;
       if (active) {
         const S* sl = slots + size_t(slot) * Q * BY * BX + ty * BX + tx;
@@ -664,7 +676,7 @@ __device__ __forceinline__ bool k1_brick(const CUtensorMap* tmap_p, const K1Args
           constexpr int a = decltype(A_)::value;
           fl[a] = load_as<S, R>(sl[a * BY * BX]);
         });
-        collide<L, R, FORCE>(fl, args.ph, own);
+        collide<L, R, FORCE>(fl, PHPLANE ? phl : args.ph, own);
         static_for<0, Q>([&](auto A_) {
           constexpr int a = decltype(A_)::value;
           if constexpr (is_lateral<L>(a)) win[lat_index<L>(a) * WPLANE + wbase] = own[a];
@@ -1018,7 +1030,8 @@ __global__ void __launch_bounds__(K1Shape<L, S, R, BX, BY, NS, WB, NXW, TS, MINB
       uint32_t* dst = reinterpret_cast<uint32_t*>(sa);
       for (int w = threadIdx.x; w < int(sizeof(K1Args<R>) / 4); w += blockDim.x) dst[w] = src[w];
       __syncthreads();
-      if (!k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE, TS, false, MINB>(tmaps + it.x, *sa, it.y, it.z, it.w))
+      if (!k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE, TS, false, MINB, true>(tmaps + it.x, *sa, it.y, it.z,
+                                                                                it.w))
         return;
     } else {
       if (!k1_brick<L, S, R, BX, BY, NS, WB, NXW, FORCE, TS, false, MINB>(tmaps + it.x, ga, it.y, it.z, it.w))
